@@ -1,0 +1,285 @@
+"""CPU oracle for stochastic texture filtering with sample reuse (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY. The tests, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg import this module; the GPU library never does. The C source in this
+directory (``stf_oracle.c``) is the oracle proper: plain C99 compiled with
+``-ffp-contract=off`` so that every float operation is rounded once, in the written order.
+
+The wrapper only marshals numpy arrays into the C structs; every step of the method runs
+in the C code. Material descriptions are plain dicts (see ``Material``) so that this module
+imports nothing from the GPU package.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "stf_oracle.c")
+HDR = os.path.join(HERE, "stf_oracle.h")
+LIB = os.path.join(HERE, "_build", "liboracle.so")
+
+BILINEAR, BSPLINE3 = 0, 1
+FULL, ONE_TAP, QUAD2, WAVE2, WAVE3, WAVE4 = 0, 1, 2, 3, 4, 5
+FP32, FP16, BF16, E4M3, UNORM8 = 0, 1, 2, 3, 4
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (one translation unit, a second or two)."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    srcs = [SRC, HDR, os.path.join(HERE, "stf_oracle_neural.c")]
+    if not force and os.path.exists(LIB):
+        if all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in srcs if os.path.exists(s)):
+            return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=gnu99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-pthread", "-o", tmp, SRC]
+    if os.path.exists(srcs[2]):
+        cmd.append(srcs[2])
+    cmd.append("-lm")
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class RefMaterial(C.Structure):
+    _fields_ = [
+        ("width", C.c_int), ("height", C.c_int), ("num_planes", C.c_int),
+        ("plane_fmt", C.c_int * 4), ("plane_ch", C.c_int * 4),
+        ("plane_data", C.c_void_p * 4),
+        ("scales", C.c_void_p), ("scale_tile", C.c_int),
+    ]
+
+
+class RefView(C.Structure):
+    _fields_ = [
+        ("width", C.c_int), ("height", C.c_int), ("H", C.c_float * 9),
+        ("cam_pos", C.c_float * 3), ("plane_to_world", C.c_float * 6), ("light_dir", C.c_float * 3),
+        ("shading", C.c_int), ("ch_albedo", C.c_int), ("ch_normal", C.c_int), ("ch_rough", C.c_int),
+        ("ch_ao", C.c_int), ("roughness", C.c_float), ("filter", C.c_int),
+        ("tile_w", C.c_int), ("tile_h", C.c_int), ("frame", C.c_int), ("view_id", C.c_int),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(LIB)
+            L.stf_ref_pcg4d.argtypes = [C.POINTER(C.c_uint32)]
+            L.stf_ref_uniforms.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                           C.POINTER(C.c_float), C.POINTER(C.c_float)]
+            L.stf_ref_weight.argtypes = [C.c_int, C.c_float]
+            L.stf_ref_weight.restype = C.c_float
+            L.stf_ref_weight_f64.argtypes = [C.c_int, C.c_double]
+            L.stf_ref_weight_f64.restype = C.c_double
+            L.stf_ref_select_axis.argtypes = [C.c_int, C.c_float, C.c_float, C.POINTER(C.c_int),
+                                              C.POINTER(C.c_float)]
+            L.stf_ref_decode.argtypes = [C.c_int, C.c_uint32]
+            L.stf_ref_decode.restype = C.c_float
+            L.stf_ref_footprint.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]
+            L.stf_ref_footprint.restype = C.c_int
+            L.stf_ref_texel_coords.argtypes = [C.POINTER(RefView), C.c_int, C.c_int, C.c_int, C.c_int,
+                                               C.POINTER(C.c_float), C.POINTER(C.c_float)]
+            L.stf_ref_shade.argtypes = [C.POINTER(RefView), C.POINTER(C.c_float), C.c_float, C.c_float,
+                                        C.POINTER(C.c_float)]
+            L.stf_ref_shade_f64.argtypes = [C.POINTER(RefView), C.POINTER(C.c_double), C.c_double,
+                                            C.c_double, C.POINTER(C.c_double)]
+            L.stf_ref_render.argtypes = [C.POINTER(RefMaterial), C.POINTER(RefView), C.c_int, C.c_uint64,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+            L.stf_ref_render.restype = C.c_int
+            L.stf_ref_render_exact_f64.argtypes = [C.POINTER(RefMaterial), C.POINTER(RefView), C.c_void_p,
+                                                   C.c_void_p, C.c_int]
+            L.stf_ref_render_exact_f64.restype = C.c_int
+            L.stf_ref_fetch_texel.argtypes = [C.POINTER(RefMaterial), C.c_int, C.c_int, C.POINTER(C.c_float)]
+            _bind_neural(L)
+            _lib = L
+    return _lib
+
+
+def _bind_neural(L):
+    if not hasattr(L, "stf_ref_mlp_forward"):
+        return
+    dp = C.c_void_p
+    L.stf_ref_neural_features.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_int, dp]
+    L.stf_ref_neural_features.restype = C.c_int
+    L.stf_ref_mlp_forward.argtypes = [dp, dp, C.c_int, dp, dp]
+    L.stf_ref_mlp_forward.restype = C.c_int
+    L.stf_ref_neural_decode.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_int, dp, dp, C.c_int, dp]
+    L.stf_ref_neural_decode.restype = C.c_int
+    L.stf_ref_neural_loss_grad.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_int, dp, C.c_int,
+                                           dp, dp, dp, dp]
+    L.stf_ref_neural_loss_grad.restype = C.c_double
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def pcg4d(v):
+    a = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in v])
+    lib().stf_ref_pcg4d(a)
+    return [int(x) for x in a]
+
+
+def uniforms(x, y, frame, view_id, seed):
+    ux, uy = C.c_float(), C.c_float()
+    lib().stf_ref_uniforms(x, y, frame, view_id, seed, C.byref(ux), C.byref(uy))
+    return ux.value, uy.value
+
+
+def weight(filt, d):
+    return lib().stf_ref_weight(filt, d)
+
+
+def weight_f64(filt, d):
+    return lib().stf_ref_weight_f64(filt, d)
+
+
+def select_axis(filt, c, u):
+    n, w = C.c_int(), C.c_float()
+    lib().stf_ref_select_axis(filt, c, u, C.byref(n), C.byref(w))
+    return n.value, w.value
+
+
+def decode(fmt, code):
+    return lib().stf_ref_decode(fmt, code)
+
+
+def footprint(mode, tw, th, lane):
+    lst = (C.c_int * 16)()
+    n = lib().stf_ref_footprint(mode, tw, th, lane, lst)
+    return [lst[i] for i in range(n)]
+
+
+def _material_struct(mat):
+    """mat: dict(width, height, planes=[(fmt, channels, ndarray)], scales=ndarray|None, scale_tile)."""
+    m = RefMaterial()
+    m.width, m.height = mat["width"], mat["height"]
+    planes = mat["planes"]
+    m.num_planes = len(planes)
+    keep = []
+    for i, (fmt, ch, arr) in enumerate(planes):
+        a = np.ascontiguousarray(arr)
+        keep.append(a)
+        m.plane_fmt[i] = fmt
+        m.plane_ch[i] = ch
+        m.plane_data[i] = a.ctypes.data
+    sc = mat.get("scales")
+    if sc is not None:
+        sc = np.ascontiguousarray(sc, dtype=np.float32)
+        keep.append(sc)
+        m.scales = sc.ctypes.data
+        m.scale_tile = int(mat["scale_tile"])
+    else:
+        m.scales = None
+        m.scale_tile = 0
+    return m, keep
+
+
+def _view_struct(view):
+    v = RefView()
+    v.width, v.height = view["width"], view["height"]
+    for i in range(9):
+        v.H[i] = float(view["H"][i])
+    for i in range(3):
+        v.cam_pos[i] = float(view.get("cam_pos", (0.0, 1.0, 0.0))[i])
+        v.light_dir[i] = float(view.get("light_dir", (0.0, 1.0, 0.0))[i])
+    for i in range(6):
+        v.plane_to_world[i] = float(view.get("plane_to_world", (1, 0, 0, 0, 1, 0))[i])
+    v.shading = int(view.get("shading", 0))
+    v.ch_albedo = int(view.get("ch_albedo", -1))
+    v.ch_normal = int(view.get("ch_normal", -1))
+    v.ch_rough = int(view.get("ch_rough", -1))
+    v.ch_ao = int(view.get("ch_ao", -1))
+    v.roughness = float(view.get("roughness", 0.3))
+    v.filter = int(view["filter"])
+    v.tile_w, v.tile_h = view.get("tile", (8, 4))
+    v.frame = int(view.get("frame", 0))
+    v.view_id = int(view.get("view_id", 0))
+    return v
+
+
+def fetch_texel(mat, x, y):
+    m, keep = _material_struct(mat)
+    out = (C.c_float * 8)()
+    lib().stf_ref_fetch_texel(C.byref(m), x, y, out)
+    del keep
+    return np.array(list(out), np.float32)
+
+
+def texel_coords(view, tex_w, tex_h, x, y):
+    v = _view_struct(view)
+    cx, cy = C.c_float(), C.c_float()
+    lib().stf_ref_texel_coords(C.byref(v), tex_w, tex_h, x, y, C.byref(cx), C.byref(cy))
+    return cx.value, cy.value
+
+
+def shade(view, ch, u, v_):
+    v = _view_struct(view)
+    a = (C.c_float * 8)(*[float(x) for x in list(ch) + [0.0] * (8 - len(ch))])
+    out = (C.c_float * 4)()
+    lib().stf_ref_shade(C.byref(v), a, u, v_, out)
+    return np.array(list(out), dtype=np.float32)
+
+
+def shade_f64(view, ch, u, v_):
+    v = _view_struct(view)
+    a = (C.c_double * 8)(*[float(x) for x in list(ch) + [0.0] * (8 - len(ch))])
+    out = (C.c_double * 4)()
+    lib().stf_ref_shade_f64(C.byref(v), a, u, v_, out)
+    return np.array(list(out), dtype=np.float64)
+
+
+def render(mat, view, mode, seed=0, nthreads=None, want_channels=False):
+    """FP32 oracle render. Returns (rgba float32 [h,w,4], idx uint32 [h,w], channels|None)."""
+    m, keep = _material_struct(mat)
+    v = _view_struct(view)
+    h, w = view["height"], view["width"]
+    out = np.zeros((h, w, 4), np.float32)
+    idx = np.zeros((h, w), np.uint32)
+    ch = np.zeros((h, w, 8), np.float32) if want_channels else None
+    nt = nthreads or os.cpu_count() or 1
+    rc = lib().stf_ref_render(C.byref(m), C.byref(v), mode, seed & (2**64 - 1), out.ctypes.data,
+                              idx.ctypes.data, ch.ctypes.data if ch is not None else None, nt)
+    if rc != 0:
+        raise ValueError("oracle render rejected its arguments (rc=%d)" % rc)
+    del keep
+    return out, idx, ch
+
+
+def render_exact_f64(mat, view, nthreads=None, want_channels=False):
+    """FP64 deterministic filter + FP64 shading (the ground truth)."""
+    m, keep = _material_struct(mat)
+    v = _view_struct(view)
+    h, w = view["height"], view["width"]
+    out = np.zeros((h, w, 4), np.float64)
+    ch = np.zeros((h, w, 8), np.float64) if want_channels else None
+    nt = nthreads or os.cpu_count() or 1
+    rc = lib().stf_ref_render_exact_f64(C.byref(m), C.byref(v), out.ctypes.data,
+                                        ch.ctypes.data if ch is not None else None, nt)
+    if rc != 0:
+        raise ValueError("oracle exact render rejected its arguments (rc=%d)" % rc)
+    del keep
+    return out, ch
+
+
+def unpack_idx(idx):
+    """Packed (ix & 0xffff) | (iy << 16) -> signed int arrays (ix, iy)."""
+    ix = (idx & 0xFFFF).astype(np.uint16).view(np.int16).astype(np.int32)
+    iy = (idx >> 16).astype(np.uint16).view(np.int16).astype(np.int32)
+    return ix, iy
+
+
+def psnr(a, ref):
+    """Linear-RGB PSNR with peak 1.0 over the RGB channels (Section 5.1 computes PSNR in linear RGB)."""
+    a = np.asarray(a, np.float64)[..., :3]
+    r = np.asarray(ref, np.float64)[..., :3]
+    mse = float(np.mean((a - r) ** 2))
+    return float("inf") if mse == 0 else 10.0 * np.log10(1.0 / mse)

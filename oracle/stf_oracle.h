@@ -1,0 +1,94 @@
+/*
+ * CPU oracle for magnified stochastic texture filtering (STF) with sample reuse,
+ * "Improved Stochastic Texture Filtering Through Sample Reuse" (Wronski, Pharr,
+ * Akenine-Moller 2025).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the GPU library includes, links or calls
+ * this code; only the test-suite, the smoke check and the benchmark's CPU-baseline
+ * leg use it. It shares no source with the CUDA path: every definition here is
+ * written out again from the paper (and, where the paper is silent, from the
+ * readings listed in the design notes).
+ *
+ * Build: plain C99, -O2 -ffp-contract=off, so that every float expression is
+ * evaluated as written (one IEEE rounding per operation, left to right).
+ */
+#ifndef STF_ORACLE_H
+#define STF_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Filters (Section 2.1; bilinear per Section S5, cubic B-spline per Section 5.5). */
+enum { REF_BILINEAR = 0, REF_BSPLINE3 = 1 };
+
+/* Sharing modes (Sections 4.3.1, 4.5; Table 1). FULL is the deterministic filter. */
+enum { REF_FULL = 0, REF_ONE_TAP = 1, REF_QUAD2 = 2, REF_WAVE2 = 3, REF_WAVE3 = 4, REF_WAVE4 = 5 };
+
+/* Stored texel formats. */
+enum { REF_FP32 = 0, REF_FP16 = 1, REF_BF16 = 2, REF_E4M3 = 3, REF_UNORM8 = 4 };
+
+#define REF_MAX_CH 8
+#define REF_MAX_PLANES 4
+
+typedef struct {
+    int width, height;             /* texels */
+    int num_planes;
+    int plane_fmt[REF_MAX_PLANES];
+    int plane_ch[REF_MAX_PLANES];  /* channels per plane; total <= 8 */
+    const void* plane_data[REF_MAX_PLANES]; /* row-major, channels interleaved */
+    const float* scales;           /* NULL, or [tiles_y][tiles_x][total channels] */
+    int scale_tile;                /* tile edge in texels when scales != NULL */
+} ref_material;
+
+typedef struct {
+    int width, height;             /* pixels */
+    float H[9];                    /* (x+.5, y+.5, 1) -> (u, v, w) projective, row-major */
+    float cam_pos[3];
+    float plane_to_world[6];       /* world x = m0 u + m1 v + m2, world z = m3 u + m4 v + m5, y = 0 */
+    float light_dir[3];            /* unit vector towards the light */
+    int shading;                   /* 0: output filtered channels 0..3; 1: Lambert + GGX */
+    int ch_albedo, ch_normal, ch_rough, ch_ao;  /* channel indices, -1 = constant */
+    float roughness;               /* used when ch_rough < 0 */
+    int filter;
+    int tile_w, tile_h;            /* warp pixel tile, tile_w * tile_h == 32 */
+    int frame, view_id;
+} ref_view;
+
+/* Counter-based hash (pcg4d, Jarzynski and Olano 2020), in place. */
+void stf_ref_pcg4d(uint32_t v[4]);
+/* The two per-pixel uniforms in [0,1) with 24-bit resolution. */
+void stf_ref_uniforms(int x, int y, int frame, int view_id, uint64_t seed, float* ux, float* uy);
+/* 1D filter weight W(d), float and double. */
+float stf_ref_weight(int filter, float d);
+double stf_ref_weight_f64(int filter, double d);
+/* Per-axis selection: lattice index and its weight (= its 1D PMF). */
+void stf_ref_select_axis(int filter, float c, float u, int* n, float* w);
+/* Texel decode of one stored value. */
+float stf_ref_decode(int fmt, uint32_t code);
+/* Decoded channels (8 slots, unused = 0) of texel (x, y), clamp-to-edge. */
+void stf_ref_fetch_texel(const ref_material* m, int x, int y, float* out);
+/* Sharing footprint of a lane: returns its size, fills list (<= 16 entries). */
+int stf_ref_footprint(int mode, int tile_w, int tile_h, int lane, int* list);
+/* Screen -> texel float coordinates of pixel (x, y) (Section 4.5 listing, first statement). */
+void stf_ref_texel_coords(const ref_view* v, int tex_w, int tex_h, int x, int y, float* cx, float* cy);
+/* Shading of filtered channels (float and double), writes rgba. */
+void stf_ref_shade(const ref_view* v, const float* ch, float u, float vv, float* rgba);
+void stf_ref_shade_f64(const ref_view* v, const double* ch, double u, double vv, double* rgba);
+
+/* FP32 render of one view: out_rgba [h][w][4]; out_idx [h][w] packed (ix & 0xffff) | (iy << 16)
+ * of the selected texel (one-tap and sharing modes), may be NULL; out_ch [h][w][8] filtered
+ * channels before shading, may be NULL. Returns 0 on success. */
+int stf_ref_render(const ref_material* m, const ref_view* v, int mode, uint64_t seed,
+                   float* out_rgba, uint32_t* out_idx, float* out_ch, int nthreads);
+
+/* FP64 exact filter (Eq. texture-continuous-sum) followed by FP64 shading: the ground truth. */
+int stf_ref_render_exact_f64(const ref_material* m, const ref_view* v, double* out_rgba,
+                             double* out_ch, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
