@@ -1,0 +1,353 @@
+"""Benchmark: magnified stochastic texture filtering with sample reuse on one 4K frame.
+
+Workload (default): 3840 x 2160 screen-aligned view at uniform 4x magnification over a
+2048 x 2048 material of 8 channels (albedo RGB, normal XY, roughness, AO, height) stored as FP16,
+bilinear filter, 3x3 wave sharing footprint in 8x4 warp tiles, Lambert + GGX shading. One step =
+one frame of the whole path (pixel -> uv, hash RNG, texel selection, fetch/decode, warp sharing,
+WIS combine, shading, store), frame index = step.
+
+Prints one JSON line. `value` is reuse-STF throughput in Gpixel/s over all ranks (replicas:
+each rank renders its own frames), timed with CUDA events on the library stream around each
+launch, L2 flushed (256 MB memset) before every timed launch. One-tap STF, the other footprints
+and the deterministic full filter are timed the same way and reported beside it, with PSNR of
+each against the full filter.
+
+--impl reference times the CPU oracle (plain C, all host cores) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/4K frame & Gpix/s: reuse-STF vs 1-sample STF vs full filter; PSNR dB"
+MODES = {"full": 0, "one_tap": 1, "quad2": 2, "wave2": 3, "wave3": 4, "wave4": 5}
+FMTS = {"fp32": 0, "fp16": 1, "bf16": 2, "e4m3": 3}
+REC_BYTES = {"fp32": 32, "fp16": 16, "bf16": 16, "e4m3": 8}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="wave3", choices=list(MODES))
+    p.add_argument("--filter", default="bilinear", choices=["bilinear", "bspline"])
+    p.add_argument("--fmt", default="fp16", choices=list(FMTS))
+    p.add_argument("--width", type=int, default=3840)
+    p.add_argument("--height", type=int, default=2160)
+    p.add_argument("--tex", type=int, default=2048)
+    p.add_argument("--no-extras", action="store_true", help="skip comparators, PSNR, e2e and CPU baseline")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def workload_config(a):
+    return {"workload": "c3-4k: %dx%d screen-aligned 4x over %dx%d 8-ch %s material, %s, %s footprint, 8x4 tiles, "
+                        "Lambert+GGX" % (a.width, a.height, a.tex, a.tex, a.fmt.upper(), a.filter, a.mode),
+            "screen": [a.width, a.height], "texture": [a.tex, a.tex, 8], "format": a.fmt, "filter": a.filter,
+            "mode": a.mode, "tile": [8, 4], "magnification": 4.0, "shading": "lambert+ggx",
+            "l2": "flushed (256 MB memset) before every timed launch"}
+
+
+def algorithmic_bytes(a):
+    """Output float4 per pixel + unique texels under the union of the filter supports."""
+    out = a.width * a.height * 16
+    sup = 1 if a.filter == "bilinear" else 3
+    vis = (a.width // 4 + sup) * (a.height // 4 + sup)
+    return out + vis * REC_BYTES[a.fmt]
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2504_05562_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu, self.proc, self.lines = gpu, None, []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        time.sleep(0.3)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_mode(stf, torch, tex, view_base, mode, steps, warmup, flush, rank, out):
+    """Per-launch CUDA-event times (ms) of `steps` frames after `warmup` frames; L2 flushed first."""
+    stream = torch.cuda.current_stream()
+    for i in range(warmup):
+        v = dict(view_base, frame=i % 65536)
+        stf.render_views([stf.make_view(v, tex, out)], stf.FILTER_PER_VIEW, mode, 0)
+    torch.cuda.synchronize()
+    times = []
+    for i in range(steps):
+        v = dict(view_base, frame=(rank * steps + i) % 65536)
+        cv = stf.make_view(v, tex, out)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stf.render_views([cv], stf.FILTER_PER_VIEW, mode, 0)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    stf.sync()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def psnr(torch, img, ref):
+    mse = torch.mean((img[..., :3].double() - ref[..., :3].double()) ** 2).item()
+    return float("inf") if mse == 0 else 10.0 * __import__("math").log10(1.0 / mse)
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def load_traffic(kernel_key):
+    """Per-launch DRAM bytes from the committed ncu summary, valid only for the same sources."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t.get(kernel_key)
+        if e and e.get("src_hash") == src_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(a, mat, view, seconds):
+    import oracle as O
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    frames = 0
+    while True:
+        O.render(mat, dict(view, frame=frames), MODES[a.mode], seed=0, nthreads=cores)
+        frames += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    px = frames * a.width * a.height
+    return {"value": px / dt / 1e9, "unit": "Gpix/s", "cores": cores, "kind": "oracle",
+            "sample": "%d full frames of the workload (%s), plain C oracle FP32 path, %d threads, %.1f s"
+                      % (frames, a.mode, cores, dt)}
+
+
+def run_reference(a):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2504_05562_gb300 import workloads as W
+    mat = W.material_c3(FMTS[a.fmt], size=a.tex)
+    filt = 0 if a.filter == "bilinear" else 1
+    view = W.config3_view(filt, width=a.width, height=a.height, tex=a.tex)
+    cores = os.cpu_count() or 1
+    for i in range(a.warmup):
+        O.render(mat, dict(view, frame=i), MODES[a.mode], seed=0, nthreads=cores)
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        O.render(mat, dict(view, frame=i), MODES[a.mode], seed=0, nthreads=cores)
+    dt = time.perf_counter() - t0
+    ms = dt * 1e3 / a.steps
+    val = a.width * a.height / (ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": val, "unit": "Gpix/s", "impl": "reference", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(a),
+            "cpu_baseline": {"value": val, "unit": "Gpix/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d full frames, plain C oracle FP32 path, %d threads" % (a.steps, cores)},
+            "e2e": {"value": val, "unit": "Gpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2504_05562_gb300 import stf
+    from paper_2504_05562_gb300 import workloads as W
+
+    mat = W.material_c3(FMTS[a.fmt], size=a.tex)
+    filt = 0 if a.filter == "bilinear" else 1
+    view = W.config3_view(filt, width=a.width, height=a.height, tex=a.tex)
+    tex = stf.Texture(mat)
+    stream = torch.cuda.current_stream()
+    stf.set_stream(stream)
+    out = torch.empty((a.height, a.width, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    mode = MODES[a.mode]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # headline: the reuse mode
+    time_mode(stf, torch, tex, view, mode, 0, a.warmup, flush, rank, out)
+    barrier()
+    with Clocks(local_rank) as clk:
+        t_wall = time.perf_counter()
+        times = time_mode(stf, torch, tex, view, mode, a.steps, 0, flush, rank, out)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    dev_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = t.item()
+    ms = dev_ms / a.steps
+    px_all = a.width * a.height * a.steps * world
+    value = px_all / (dev_ms * 1e-3) / 1e9
+
+    alg = algorithmic_bytes(a)
+    peaks = load_peaks()
+    peak = peaks.get("hbm_gbs")
+    kernel_key = "k_render_view/%s/%s/%s" % (a.fmt, a.filter, a.mode)
+    roof = {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak if peak else 6800.0,
+            "unit": "GB/s", "peak_source": "measured" if peak else "fallback",
+            "traffic": load_traffic(kernel_key), "algorithmic_bytes_per_launch": alg}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+
+    line = {"metric": METRIC, "value": value, "unit": "Gpix/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(a),
+            "roofline": roof, "gpu_launches": a.steps, "clocks": clk.summary(),
+            "ms_per_frame": {"min": min(times), "median": statistics.median(times), "max": max(times)},
+            "wall_s_timed_region": t_wall}
+
+    if not a.no_extras and rank == 0:
+        extras = {}
+        refs = {}
+        for name, m in MODES.items():
+            tt = time_mode(stf, torch, tex, view, m, max(5, a.steps // 2), 3, flush, rank, out)
+            med = statistics.median(tt)
+            extras[name] = {"ms_median": med, "gpix_s": a.width * a.height / (med * 1e-3) / 1e9}
+            img = torch.empty_like(out)
+            stf.render_views([stf.make_view(dict(view, frame=0), tex, img)], stf.FILTER_PER_VIEW, m, 0)
+            refs[name] = img
+        torch.cuda.synchronize()
+        for name in MODES:
+            extras[name]["psnr_db_vs_full"] = psnr(torch, refs[name], refs["full"]) if name != "full" else None
+        line["modes"] = extras
+        line["reuse_time_over_one_tap"] = extras[a.mode]["ms_median"] / extras["one_tap"]["ms_median"]
+        line["e2e"] = e2e(a, stf, torch, mat, view)
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(a, mat, view, a.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tex.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(a, stf, torch, mat, view):
+    """Through the public API with host buffers: upload the material from pinned host memory
+    (texture creation), render, read the frame back into pinned host memory; per step."""
+    import numpy as np
+    plane = mat["planes"][0]
+    host = torch.from_numpy(np.ascontiguousarray(plane[2]).view(np.uint8).reshape(-1)).pin_memory()
+    hmat = dict(mat, planes=[(plane[0], plane[1], host.numpy())])
+    out = torch.empty((a.height, a.width, 4), dtype=torch.float32, device="cuda")
+    host_out = torch.empty((a.height, a.width, 4), dtype=torch.float32).pin_memory()
+    steps = max(3, a.steps // 2)
+    for i in range(2):
+        t = stf.Texture(hmat)
+        stf.render_views([stf.make_view(dict(view, frame=i), t, out)], stf.FILTER_PER_VIEW, MODES[a.mode], 0)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        t.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        t = stf.Texture(hmat)
+        stf.render_views([stf.make_view(dict(view, frame=i), t, out)], stf.FILTER_PER_VIEW, MODES[a.mode], 0)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        t.close()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": a.width * a.height / dt / 1e9, "unit": "Gpix/s", "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": int(host.numel()) + 200, "d2h_bytes_per_step": int(host_out.numel() * 4)}
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

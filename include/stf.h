@@ -1,0 +1,176 @@
+/*
+ * stf.h - C interface of the GB300 library for magnified stochastic texture filtering (STF)
+ * with sample reuse ("Improved Stochastic Texture Filtering Through Sample Reuse",
+ * Wronski, Pharr, Akenine-Moller, 2025).
+ *
+ * The problem (Section 2.1, Eq. texture-continuous-sum): for each pixel, estimate the filtered
+ * texture value sum_i f_r(u - u_i, v - v_i) T_i at the pixel's texture coordinate, then shade.
+ * The library estimates it the paper's way: each pixel draws ONE texel with probability equal
+ * to its filter weight (one-tap STF, Eq. mc-estimator and Section S1), the pixels of a 32-lane
+ * warp tile share their texels with warp shuffles (Section 4.3, Section 4.5), and each pixel
+ * combines the shared texels with the bounded weighted importance sampling estimator
+ * w_i = f_c(x_i) / f_i(x_i), result = sum_i w_i T_i / sum_j w_j (Eqs. bart-weighted-estimator,
+ * estimator-for-stf and estimator-convex, Section 4.2).
+ *
+ * Conventions for every entry point:
+ *   - Functions return stf_status; no C++ exception crosses the interface.
+ *   - On a non-OK status, stf_last_error() returns a message for the calling thread.
+ *   - Work is enqueued asynchronously on the stream set with stf_set_stream (default: the
+ *     legacy default stream). Device-side error flags are reported by stf_sync() and by the
+ *     next stf_render_views() call.
+ *   - Pointers documented as "device" must be CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary CPU memory.
+ *   - Not thread-safe: callers serialise calls that share a stream or a texture.
+ */
+#ifndef STF_H
+#define STF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    STF_OK = 0,
+    STF_ERR_INVALID_ARG = 1,   /* rejected on the host, nothing enqueued */
+    STF_ERR_UNSUPPORTED = 2,   /* a valid request this build does not implement */
+    STF_ERR_OUT_OF_MEMORY = 3, /* a device allocation failed */
+    STF_ERR_CUDA = 4,          /* a CUDA runtime call failed; the message names it */
+    STF_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up (persistent scheduler) */
+    STF_ERR_DEVICE_ASSERT = 6  /* a device-side check recorded an out-of-range index */
+} stf_status;
+
+/* Reconstruction filters: bilinear (tent) per Section S5; uniform cubic B-spline per Section
+ * 5.5. STF_FILTER_PER_VIEW takes stf_view.filter for each view. */
+typedef enum { STF_FILTER_BILINEAR = 0, STF_FILTER_BSPLINE3 = 1, STF_FILTER_PER_VIEW = -1 } stf_filter;
+
+/* Estimators:
+ *   FULL     deterministic filter, every texel under the filter fetched and weighted (the
+ *            comparator of Section 5.7);
+ *   ONE_TAP  one-tap STF, the texel drawn by the pixel itself (Section 2.2);
+ *   QUAD2    sharing inside aligned 2x2 pixel quads (Table 1 "2x2q");
+ *   WAVE2/3/4 square k x k sharing footprints placed per lane inside the warp tile (Section
+ *            4.3.1; Table 1 "2x2w", "3x3", "4x4"). On a 16x2 tile the k x k block becomes
+ *            min(k,2) rows by round(k*k/2) columns. */
+typedef enum {
+    STF_MODE_FULL = 0, STF_MODE_ONE_TAP = 1, STF_MODE_QUAD2 = 2,
+    STF_MODE_WAVE2 = 3, STF_MODE_WAVE3 = 4, STF_MODE_WAVE4 = 5
+} stf_reuse_mode;
+
+/* Stored texel formats. FP16 = IEEE binary16, BF16 = bfloat16, E4M3 = OCP FP8 E4M3 ("FN"),
+ * UNORM8 = q / 255. NEURAL = texels decoded by a small MLP from a latent grid (see
+ * stf_decoder_*). */
+typedef enum {
+    STF_FMT_FP32 = 0, STF_FMT_FP16 = 1, STF_FMT_BF16 = 2, STF_FMT_E4M3 = 3, STF_FMT_UNORM8 = 4,
+    STF_FMT_NEURAL = 5
+} stf_format;
+
+typedef struct stf_texture stf_texture; /* opaque, library-owned */
+typedef struct stf_decoder stf_decoder; /* opaque, library-owned */
+
+/* One plane of a material: `channels` values of format `fmt` per texel, texels row-major,
+ * channels interleaved. `data` is host memory unless data_on_device != 0. */
+typedef struct {
+    int fmt;
+    int channels;
+    const void* data;
+    int data_on_device;
+} stf_plane;
+
+/* A material: 1..4 planes sharing one width x height (max 16384 x 16384), 1..8 channels in
+ * total, numbered across planes in order. Optional per-(tile, channel) FP32 scales multiply
+ * the decoded value: tile_scales[(ty * tiles_x + tx) * channels + c] with tiles of scale_tile x
+ * scale_tile texels (tiles_x = ceil(width / scale_tile)); pass NULL for none. For a NEURAL
+ * material set num_planes = 0 and `decoder`. */
+typedef struct {
+    int width, height;
+    int num_planes;
+    stf_plane planes[4];
+    const float* tile_scales;
+    int scale_tile;
+    int scales_on_device;
+    const stf_decoder* decoder;
+} stf_texture_desc;
+
+/* One view (one output image). The pixel centre (x + 0.5, y + 0.5, 1) is mapped by the
+ * row-major projective matrix H to (hu, hv, hw); uv = (hu / hw, hv / hw) in [0, 1]^2 spans the
+ * texture (an analytic stand-in for the paper's G-buffer UVs, Section 5). Texel float
+ * coordinates are uv * size - 0.5 (Section 4.5 listing). Addressing is clamp-to-edge.
+ *
+ * Shading (shading = 1) runs after the estimate, on the filtered channels: Lambert plus GGX
+ * (Smith height-correlated visibility, Schlick Fresnel with F0 = 0.04) lit by one directional
+ * light of irradiance pi from light_dir (unit, towards the light). The ground plane is y = 0 with
+ * tangent frame T = +x, B = +z, N = +y; a pixel's world point is (m0 u + m1 v + m2, 0,
+ * m3 u + m4 v + m5) with m = plane_to_world. Channel map: ch_albedo (3 channels), ch_normal
+ * (tangent-space X, Y; Z reconstructed), ch_rough (else `roughness`), ch_ao (else 1); -1 means
+ * absent. shading = 0 writes the filtered channels 0..3 (missing ones 0, alpha 1).
+ *
+ * tile_w x tile_h is the warp's pixel tile: 8x4, 4x8 or 16x2, or 0x0 to let the library pick.
+ * Outputs: out_rgba (device, float4 per pixel, row pitch out_pitch_floats floats, 0 = 4 *
+ * width) is written for every on-screen pixel. debug_indices (device, optional, width * height
+ * uint32) receives the selected texel as (ix & 0xffff) | (iy << 16) (unclamped lattice
+ * coordinates; 0 in FULL mode). debug_channels (device, optional, width * height * 8 floats)
+ * receives the filtered channels before shading. The random stream of a pixel is keyed by
+ * (x, y, frame | view_id << 16, seed); frame and view_id must be below 65536. */
+typedef struct {
+    int width, height;
+    float H[9];
+    float cam_pos[3];
+    float plane_to_world[6];
+    float light_dir[3];
+    int shading;
+    int ch_albedo, ch_normal, ch_rough, ch_ao;
+    float roughness;
+    int filter;
+    int tile_w, tile_h;
+    int frame;
+    int view_id;
+    const stf_texture* tex;
+    float* out_rgba;
+    long long out_pitch_floats;
+    uint32_t* debug_indices;
+    float* debug_channels;
+} stf_view;
+
+/* Creates a texture from a material description (Section 2.1, Eq. texture-definition: a texel
+ * lattice). The library copies the texels into its own device memory, interleaving all planes
+ * of a texel into one record of 4, 8, 16 or 32 bytes; stf_destroy frees it. Formats are kept
+ * as stored (FP16 stays FP16 in device memory) where a dedicated kernel exists; any other
+ * combination is widened to FP32 at creation, which is exact because every decode is.
+ * Errors: STF_ERR_INVALID_ARG for a bad description (the message says which field),
+ * STF_ERR_OUT_OF_MEMORY, STF_ERR_CUDA. *out is set only on success. Synchronous. */
+stf_status stf_create_texture(const stf_texture_desc* desc, stf_texture** out);
+
+/* Renders n views (host array `views`, n >= 1) with one estimator for all of them.
+ * `filter` is STF_FILTER_BILINEAR / STF_FILTER_BSPLINE3 for every view, or STF_FILTER_PER_VIEW.
+ * `reuse_mode` is an stf_reuse_mode. `seed` keys the counter-based random stream (pcg4d of
+ * Jarzynski and Olano 2020) together with each pixel's (x, y, frame, view_id).
+ * Each view's texture must outlive the enqueued work. Every view is validated before anything
+ * is enqueued; on STF_ERR_INVALID_ARG no output is touched. Several views are rendered by one
+ * persistent launch that pulls (view, tile range) items from a device queue.
+ * Asynchronous on the library stream. */
+stf_status stf_render_views(const stf_view* views, int n, int filter, int reuse_mode,
+                            unsigned long long seed);
+
+/* Frees a texture (NULL is a no-op). The caller ensures no enqueued work still reads it. */
+stf_status stf_destroy(stf_texture* tex);
+
+/* Sets the CUDA stream (a cudaStream_t passed as void*) for all later work; NULL = legacy
+ * default stream. */
+stf_status stf_set_stream(void* cuda_stream);
+
+/* Waits for the library stream and reports device-side error flags (STF_ERR_TIMEOUT,
+ * STF_ERR_DEVICE_ASSERT), clearing them. */
+stf_status stf_sync(void);
+
+/* Message for the last non-OK status on the calling thread ("" if none). */
+const char* stf_last_error(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int stf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STF_H */

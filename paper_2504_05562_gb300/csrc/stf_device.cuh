@@ -1,0 +1,395 @@
+// Device side of the STF render path: per-view constants, texel formats, the per-axis
+// selection, the warp-tile sharing loop with the weighted importance sampling combine, and
+// shading. Everything a render kernel needs is a __forceinline__ function of this header;
+// the kernels themselves are instantiated in stf_kernels.cuh.
+//
+// Bit-exactness contract with the CPU oracle: the choice of texel (the screen -> texel
+// coordinates, the 1D filter weights, the running CDF and the comparison with the uniform)
+// is computed with explicitly rounded intrinsics (__fmul_rn / __fadd_rn / __fdiv_rn), which
+// the compiler never contracts into FMAs, in the same order as the oracle. The colour path
+// (weights w_i, sums, shading) may use FMAs and fast reciprocals.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+namespace stf {
+
+constexpr float kCoordLo = -16384.0f;  // texel coordinates are clamped to [lo, hi] (NaN -> lo)
+constexpr float kCoordHi = 32000.0f;
+constexpr float kPi = 3.14159265f;
+constexpr int kMaxCh = 8;
+
+// Material kinds with a dedicated kernel. Anything else is widened to FP32 at creation.
+enum MatKind : int {
+    K_F32x4 = 0,      // RGBA FP32, 16-byte records
+    K_F32x8 = 1,      // 8 x FP32, 32-byte records
+    K_F16x4 = 2,      // 4 x FP16, 8-byte records
+    K_F16x8 = 3,      // 8 x FP16, 16-byte records
+    K_BF16x8 = 4,     // 8 x BF16, 16-byte records
+    K_E4M3x8 = 5,     // 8 x E4M3 with per-(tile, channel) FP32 scales, 8-byte records
+    K_U8x4_F16x2 = 6, // RGBA UNORM8 + XY FP16, 8-byte records
+    K_NEURAL = 7,     // latent grid + MLP decoder
+    K_COUNT = 8
+};
+
+// Per-view constants, passed by value (kernel parameter space) or read from a device array
+// by the multi-view scheduler.
+struct DevView {
+    float H[9];
+    float cam[3];
+    float p2w[6];
+    float light[3];
+    float rough_const;
+    int width, height;
+    int tiles_x, tiles_y;
+    int tex_w, tex_h;
+    float tex_wf, tex_hf;
+    const void* texels;
+    const float* scales;
+    const float* unorm_lut;   // 256 entries q / 255 (IEEE), for UNORM8 planes
+    int scale_shift, scale_tiles_x;
+    float* out;
+    long long pitch;          // floats per output row
+    uint32_t* dbg_idx;
+    float* dbg_ch;
+    uint32_t rng_z, rng_w;    // frame | view_id << 16, and the folded 64-bit seed
+    int shade_layout;         // 0 none, 1 = (albedo 0, normal 3, rough 5, ao 6), 2 = (albedo 0, normal 4), 3 generic
+    int ch_albedo, ch_normal, ch_rough, ch_ao;
+    int c_true;               // channels of the material (alpha default when < 4)
+    int filter, tile_w, tile_h;
+    const void* neural;       // decoder parameters for K_NEURAL
+};
+
+// ------------------------------------------------------------------------------ RNG
+
+// pcg4d (Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020): LCG step on the
+// four words, cross multiply-add round, xor-shift by 16, second cross multiply-add round.
+__device__ __forceinline__ void pcg4d(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d)
+{
+    a = a * 1664525u + 1013904223u;
+    b = b * 1664525u + 1013904223u;
+    c = c * 1664525u + 1013904223u;
+    d = d * 1664525u + 1013904223u;
+    a += b * d; b += c * a; c += a * b; d += b * c;
+    a ^= a >> 16; b ^= b >> 16; c ^= c >> 16; d ^= d >> 16;
+    a += b * d; b += c * a; c += a * b; d += b * c;
+}
+
+// ------------------------------------------------------------------------------ filters
+
+template <int F> struct Taps;
+template <> struct Taps<0> { static constexpr int N = 2, K0 = 0; };   // bilinear: floor(c) + {0, 1}
+template <> struct Taps<1> { static constexpr int N = 4, K0 = -1; };  // cubic B-spline: floor(c) + {-1..2}
+
+// Bilinear tent per axis, clamp(1 - |d|, 0, 1) (Section S5). 1 - |d| never exceeds 1.
+__device__ __forceinline__ float w_bilinear(float d)
+{
+    return fmaxf(__fsub_rn(1.0f, fabsf(d)), 0.0f);
+}
+
+// Uniform cubic B-spline per axis with a = |d|: ((3a - 6) a) a + 4 over 6 for a < 1,
+// (2 - a)^3 / 6 for a < 2, else 0; each step rounded once, "/ 6" as a multiply by the float
+// nearest 1/6.
+__device__ __forceinline__ float w_bspline(float d)
+{
+    const float a = fabsf(d);
+    float t = __fmul_rn(3.0f, a);
+    t = __fsub_rn(t, 6.0f);
+    t = __fmul_rn(t, a);
+    t = __fmul_rn(t, a);
+    t = __fadd_rn(t, 4.0f);
+    const float r1 = __fmul_rn(t, 1.0f / 6.0f);
+    const float s = __fsub_rn(2.0f, a);
+    float q = __fmul_rn(s, s);
+    q = __fmul_rn(q, s);
+    const float r2 = __fmul_rn(q, 1.0f / 6.0f);
+    return a < 1.0f ? r1 : (a < 2.0f ? r2 : 0.0f);
+}
+
+template <int F> __device__ __forceinline__ float wfun(float d)
+{
+    return F == 0 ? w_bilinear(d) : w_bspline(d);
+}
+
+// One axis of a lane: its lattice base, the weights of its taps, and its one-tap selection.
+template <int F> struct Axis {
+    int base;                  // floor(c) + K0: lattice index of tap 0
+    float w[Taps<F>::N];       // W(c - (base + t))
+    int n;                     // selected lattice index
+    float p;                   // its weight (the 1D PMF value)
+};
+
+// Taps in increasing lattice order; running FP32 CDF; first tap with u < CDF, else the last
+// tap with positive weight.
+template <int F> __device__ __forceinline__ void axis_select(float c, float u, Axis<F>& A)
+{
+    constexpr int NT = Taps<F>::N;
+    const int i0 = __float2int_rd(c);
+    A.base = i0 + Taps<F>::K0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) A.w[t] = wfun<F>(__fsub_rn(c, __int2float_rn(A.base + t)));
+    float cdf = 0.0f;
+    int pick = -1;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        cdf = __fadd_rn(cdf, A.w[t]);
+        if (pick < 0 && u < cdf) pick = t;
+    }
+#pragma unroll
+    for (int t = NT - 1; t >= 0; --t)
+        if (pick < 0 && A.w[t] > 0.0f) pick = t;
+    float p = A.w[0];
+#pragma unroll
+    for (int t = 1; t < NT; ++t) p = (pick == t) ? A.w[t] : p;
+    A.n = A.base + pick;
+    A.p = p;
+}
+
+// Tap weights only (for the deterministic filter).
+template <int F> __device__ __forceinline__ void axis_weights(float c, Axis<F>& A)
+{
+    const int i0 = __float2int_rd(c);
+    A.base = i0 + Taps<F>::K0;
+#pragma unroll
+    for (int t = 0; t < Taps<F>::N; ++t) A.w[t] = wfun<F>(__fsub_rn(c, __int2float_rn(A.base + t)));
+}
+
+// W(c - n) for another lane's lattice index n, read from this lane's tap weights: the taps are
+// the only lattice points with non-zero weight, and for them the value is the same rounded
+// expression as the selection used.
+template <int F> __device__ __forceinline__ float axis_weight_of(const Axis<F>& A, int n)
+{
+    const int k = n - A.base;
+    float r = 0.0f;
+#pragma unroll
+    for (int t = 0; t < Taps<F>::N; ++t) r = (k == t) ? A.w[t] : r;
+    return r;
+}
+
+// ------------------------------------------------------------------------------ coordinates
+
+// Pixel centre -> uv through the view homography, rounded step by step like the oracle.
+__device__ __forceinline__ void pixel_uv(const DevView& v, int x, int y, float& u, float& w)
+{
+    const float px = __fadd_rn(__int2float_rn(x), 0.5f);
+    const float py = __fadd_rn(__int2float_rn(y), 0.5f);
+    const float hx = __fadd_rn(__fadd_rn(__fmul_rn(v.H[0], px), __fmul_rn(v.H[1], py)), v.H[2]);
+    const float hy = __fadd_rn(__fadd_rn(__fmul_rn(v.H[3], px), __fmul_rn(v.H[4], py)), v.H[5]);
+    const float hw = __fadd_rn(__fadd_rn(__fmul_rn(v.H[6], px), __fmul_rn(v.H[7], py)), v.H[8]);
+    u = __fdiv_rn(hx, hw);
+    w = __fdiv_rn(hy, hw);
+}
+
+// uv * size - 0.5 (Section 4.5 listing), clamped so lattice indices fit 16 bits.
+__device__ __forceinline__ float texel_coord(float uv, float size)
+{
+    const float c = __fsub_rn(__fmul_rn(uv, size), 0.5f);
+    return fminf(fmaxf(c, kCoordLo), kCoordHi);
+}
+
+__device__ __forceinline__ uint32_t pack_idx(int ix, int iy)
+{
+    return (uint32_t)(ix & 0xffff) | ((uint32_t)(iy & 0xffff) << 16);
+}
+__device__ __forceinline__ int unpack_x(uint32_t p) { return (int)(int16_t)(p & 0xffffu); }
+__device__ __forceinline__ int unpack_y(uint32_t p) { return ((int)p) >> 16; }
+
+// ------------------------------------------------------------------------------ texel formats
+
+__device__ __forceinline__ int clampi(int a, int lo, int hi) { return min(max(a, lo), hi); }
+
+__device__ __forceinline__ float h2f(uint32_t bits16) { return __half2float(__ushort_as_half((unsigned short)bits16)); }
+__device__ __forceinline__ float bf2f(uint32_t bits16) { return __uint_as_float(bits16 << 16); }
+
+template <int KIND> struct Mat;
+
+template <> struct Mat<K_F32x4> {
+    static constexpr int C = 4;
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        const float4 r = __ldg(reinterpret_cast<const float4*>(v.texels) + ((size_t)y * v.tex_w + x));
+        t[0] = r.x; t[1] = r.y; t[2] = r.z; t[3] = r.w;
+    }
+};
+
+template <> struct Mat<K_F32x8> {
+    static constexpr int C = 8;
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        const float4* p = reinterpret_cast<const float4*>(v.texels) + 2 * ((size_t)y * v.tex_w + x);
+        const float4 a = __ldg(p), b = __ldg(p + 1);
+        t[0] = a.x; t[1] = a.y; t[2] = a.z; t[3] = a.w; t[4] = b.x; t[5] = b.y; t[6] = b.z; t[7] = b.w;
+    }
+};
+
+template <> struct Mat<K_F16x4> {
+    static constexpr int C = 4;
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        const uint2 r = __ldg(reinterpret_cast<const uint2*>(v.texels) + ((size_t)y * v.tex_w + x));
+        t[0] = h2f(r.x & 0xffffu); t[1] = h2f(r.x >> 16); t[2] = h2f(r.y & 0xffffu); t[3] = h2f(r.y >> 16);
+    }
+};
+
+template <> struct Mat<K_F16x8> {
+    static constexpr int C = 8;
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        const uint4 r = __ldg(reinterpret_cast<const uint4*>(v.texels) + ((size_t)y * v.tex_w + x));
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { t[2 * i] = h2f(w[i] & 0xffffu); t[2 * i + 1] = h2f(w[i] >> 16); }
+    }
+};
+
+template <> struct Mat<K_BF16x8> {
+    static constexpr int C = 8;
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        const uint4 r = __ldg(reinterpret_cast<const uint4*>(v.texels) + ((size_t)y * v.tex_w + x));
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { t[2 * i] = bf2f(w[i] & 0xffffu); t[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u); }
+    }
+};
+
+template <> struct Mat<K_E4M3x8> {
+    static constexpr int C = 8;
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        const uint2 r = __ldg(reinterpret_cast<const uint2*>(v.texels) + ((size_t)y * v.tex_w + x));
+        const float4* sp = reinterpret_cast<const float4*>(
+            v.scales + ((size_t)(y >> v.scale_shift) * v.scale_tiles_x + (x >> v.scale_shift)) * 8);
+        const float4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
+        const float s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+        const uint32_t w[2] = {r.x, r.y};
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> (16 * j)), __NV_E4M3);
+                const float lo = __half2float(__half(__half_raw{h2.x}));
+                const float hi = __half2float(__half(__half_raw{h2.y}));
+                t[4 * i + 2 * j] = __fmul_rn(lo, s[4 * i + 2 * j]);
+                t[4 * i + 2 * j + 1] = __fmul_rn(hi, s[4 * i + 2 * j + 1]);
+            }
+        }
+    }
+};
+
+template <> struct Mat<K_U8x4_F16x2> {
+    static constexpr int C = 8;  // 6 used; channels 6 and 7 read as 0
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        const uint2 r = __ldg(reinterpret_cast<const uint2*>(v.texels) + ((size_t)y * v.tex_w + x));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) t[i] = __ldg(v.unorm_lut + ((r.x >> (8 * i)) & 255u));
+        t[4] = h2f(r.y & 0xffffu);
+        t[5] = h2f(r.y >> 16);
+        t[6] = 0.0f;
+        t[7] = 0.0f;
+    }
+};
+
+// ------------------------------------------------------------------------------ shading
+
+// Lambert + GGX after filtering; see the interface header for the conventions. The GGX
+// denominator uses a^2 (N.H)^2 + |N x H|^2 (equal to (N.H)^2 (a^2 - 1) + 1 for unit vectors),
+// which keeps the specular peak well conditioned in FP32.
+__device__ __forceinline__ float4 shade(const DevView& v, float r0, float r1, float r2, float nx, float ny,
+                                        float rough, float ao, float u, float w)
+{
+    const float z2 = 1.0f - nx * nx - ny * ny;
+    const float nz = sqrtf(fmaxf(z2, 0.0f));
+    const float inl = rsqrtf(nx * nx + nz * nz + ny * ny);
+    const float N0 = nx * inl, N1 = nz * inl, N2 = ny * inl;  // world (x, y, z) = (T, N, B)
+    rough = fmaxf(rough, 0.02f);
+    const float P0 = v.p2w[0] * u + v.p2w[1] * w + v.p2w[2];
+    const float P2 = v.p2w[3] * u + v.p2w[4] * w + v.p2w[5];
+    float V0 = v.cam[0] - P0, V1 = v.cam[1], V2 = v.cam[2] - P2;
+    const float ivl = rsqrtf(V0 * V0 + V1 * V1 + V2 * V2);
+    V0 *= ivl; V1 *= ivl; V2 *= ivl;
+    const float L0 = v.light[0], L1 = v.light[1], L2 = v.light[2];
+    const float NL = N0 * L0 + N1 * L1 + N2 * L2;
+    if (!(NL > 0.0f)) return make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+    const float NV = fmaxf(N0 * V0 + N1 * V1 + N2 * V2, 1e-4f);
+    float H0 = L0 + V0, H1 = L1 + V1, H2 = L2 + V2;
+    const float ihl = rsqrtf(H0 * H0 + H1 * H1 + H2 * H2);
+    H0 *= ihl; H1 *= ihl; H2 *= ihl;
+    const float NH = fmaxf(N0 * H0 + N1 * H1 + N2 * H2, 0.0f);
+    const float VH = fmaxf(V0 * H0 + V1 * H1 + V2 * H2, 0.0f);
+    const float c0 = N1 * H2 - N2 * H1, c1 = N2 * H0 - N0 * H2, c2 = N0 * H1 - N1 * H0;
+    const float s2 = c0 * c0 + c1 * c1 + c2 * c2;
+    const float al = rough * rough;
+    const float a2 = al * al;
+    const float t = a2 * NH * NH + s2;
+    const float D = a2 / (kPi * t * t);
+    const float gv = NL * sqrtf(NV * NV * (1.0f - a2) + a2);
+    const float gl = NV * sqrtf(NL * NL * (1.0f - a2) + a2);
+    const float Vis = 0.5f / (gv + gl);
+    const float q = 1.0f - VH;
+    const float q2 = q * q;
+    const float F = 0.04f + 0.96f * (q2 * q2 * q);
+    const float ps = kPi * D * Vis * F;
+    const float k = ao * NL;
+    return make_float4(k * (r0 + ps), k * (r1 + ps), k * (r2 + ps), 1.0f);
+}
+
+template <int C> __device__ __forceinline__ float pick_ch(const float (&f)[C], int idx)
+{
+    float r = 0.0f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) r = (idx == c) ? f[c] : r;
+    return r;
+}
+
+template <int C> __device__ __forceinline__ float4 finish_pixel(const DevView& v, const float (&f)[C], float u, float w)
+{
+    if (v.shade_layout == 0) {
+        float o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = (k < C && k < v.c_true) ? f[k < C ? k : 0] : (k == 3 ? 1.0f : 0.0f);
+        return make_float4(o[0], o[1], o[2], o[3]);
+    }
+    if constexpr (C >= 7) {
+        if (v.shade_layout == 1) return shade(v, f[0], f[1], f[2], f[3], f[4], f[5], f[6], u, w);
+        if (v.shade_layout == 2) return shade(v, f[0], f[1], f[2], f[4], f[5], v.rough_const, 1.0f, u, w);
+    }
+    // generic channel map (uniform per view)
+    const float r0 = v.ch_albedo >= 0 ? pick_ch(f, v.ch_albedo) : 1.0f;
+    const float r1 = v.ch_albedo >= 0 ? pick_ch(f, v.ch_albedo + 1) : 1.0f;
+    const float r2 = v.ch_albedo >= 0 ? pick_ch(f, v.ch_albedo + 2) : 1.0f;
+    const float nx = v.ch_normal >= 0 ? pick_ch(f, v.ch_normal) : 0.0f;
+    const float ny = v.ch_normal >= 0 ? pick_ch(f, v.ch_normal + 1) : 0.0f;
+    const float ro = v.ch_rough >= 0 ? pick_ch(f, v.ch_rough) : v.rough_const;
+    const float ao = v.ch_ao >= 0 ? pick_ch(f, v.ch_ao) : 1.0f;
+    return shade(v, r0, r1, r2, nx, ny, ro, ao, u, w);
+}
+
+// ------------------------------------------------------------------------------ footprints
+
+// Source-lane block of the sharing footprint (row-major kx x ky block at (ox, oy)); the same
+// placement rule as the oracle: QUAD2 = aligned 2x2; WAVEk = ky = min(k, TH) rows,
+// kx = min(TW, round(k^2 / ky)) columns, centred on the lane and shifted inside the tile.
+template <int MODE, int TW, int TH> struct Footprint {
+    static constexpr int k = MODE == 3 ? 2 : (MODE == 4 ? 3 : (MODE == 5 ? 4 : 2));
+    static constexpr int KY = MODE == 2 ? 2 : (k < TH ? k : TH);
+    static constexpr int KXr = MODE == 2 ? 2 : (k * k + KY / 2) / KY;
+    static constexpr int KX = KXr < TW ? KXr : TW;
+    static constexpr int N = KX * KY;
+    __device__ static __forceinline__ int base(int lx, int ly)
+    {
+        int ox, oy;
+        if (MODE == 2) { ox = lx & ~1; oy = ly & ~1; }
+        else {
+            ox = min(max(lx - (KX - 1) / 2, 0), TW - KX);
+            oy = min(max(ly - (KY - 1) / 2, 0), TH - KY);
+        }
+        return oy * TW + ox;
+    }
+};
+
+}  // namespace stf

@@ -1,0 +1,35 @@
+// Host-side internals shared by the library's translation units (not part of the C interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+
+#include "stf.h"
+#include "stf_device.cuh"
+
+struct stf_texture {
+    int width, height, channels;
+    int kind;                       // stf::MatKind
+    void* texels;                   // device records
+    float* scales;                  // device, E4M3 kind only
+    int scale_shift, scale_tiles_x;
+    const stf_decoder* decoder;     // NEURAL kind
+    const void* decoder_params;     // device parameter block of the decoder (NEURAL kind)
+};
+
+stf_status stf_fail(stf_status s, const char* fmt, ...);
+stf_status stf_cuda_fail(cudaError_t e, const char* what);
+cudaStream_t stf_stream();
+stf_status stf_device_state(int** flags, const float** lut);
+stf_status stf_validate_view(const stf_view& v, int i, int filter, int mode);
+void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long long seed, const float* lut,
+                      stf::DevView& d);
+cudaError_t stf_launch_single(const stf::DevView& d, int kind, int mode, cudaStream_t s);
+
+// multi-view scheduler (stf_sched.cu)
+stf_status stf_render_batch(const stf_view* views, int n, int filter, int mode, unsigned long long seed);
+
+// neural decoder (stf_neural.cu)
+stf_status stf_create_neural_texture(const stf_texture_desc* d, stf_texture** out);
+cudaError_t stf_launch_neural_view(const stf::DevView& d, int mode, cudaStream_t s);

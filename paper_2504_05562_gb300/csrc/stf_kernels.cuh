@@ -1,0 +1,139 @@
+// Render kernels. One warp renders one TW x TH pixel tile (lane = ly * TW + lx), which is the
+// paper's wave-to-pixel mapping with linear row lane order (Section 2.3, Figure "wave"); texels
+// are exchanged with __shfl_sync, the CUDA counterpart of WaveReadLaneAt (Section 4.5).
+#pragma once
+
+#include <float.h>
+
+#include "stf_device.cuh"
+#include "stf_neural_device.cuh"
+
+namespace stf {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int KIND> struct Channels { static constexpr int C = Mat<KIND>::C; };
+template <> struct Channels<K_NEURAL> { static constexpr int C = 8; };
+
+// Fetch or decode one texel of lattice point (x, y) with clamp-to-edge addressing.
+// For K_NEURAL all 32 lanes must call it together (the decode is a warp-wide matrix product).
+template <int KIND>
+__device__ __forceinline__ void fetch_texel(const DevView& v, int x, int y, float (&t)[Channels<KIND>::C])
+{
+    x = clampi(x, 0, v.tex_w - 1);
+    y = clampi(y, 0, v.tex_h - 1);
+    if constexpr (KIND == K_NEURAL) neural_decode_warp(v, x, y, t);
+    else Mat<KIND>::fetch(v, x, y, t);
+}
+
+// One warp tile of one view. MODE: 0 full filter, 1 one-tap, 2 quad 2x2, 3..5 wave k x k.
+// All 32 lanes execute every shuffle (off-screen lanes of a partial tile compute with
+// extrapolated coordinates and only skip the store).
+template <int KIND, int F, int MODE, int TW, int TH>
+__device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane)
+{
+    constexpr int C = Channels<KIND>::C;
+    const int lx = lane % TW, ly = lane / TW;
+    const int x = tx * TW + lx, y = ty * TH + ly;
+    float u, w;
+    pixel_uv(v, x, y, u, w);
+    const float cx = texel_coord(u, v.tex_wf);
+    const float cy = texel_coord(w, v.tex_hf);
+    float res[C];
+    uint32_t pk = 0;
+
+    if constexpr (MODE == 0) {
+        // deterministic filter: sum over taps of W(dx) W(dy) T, y outer (Eq. texture-continuous-sum)
+        Axis<F> ax, ay;
+        axis_weights<F>(cx, ax);
+        axis_weights<F>(cy, ay);
+#pragma unroll
+        for (int c = 0; c < C; ++c) res[c] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < Taps<F>::N; ++s) {
+#pragma unroll
+            for (int t = 0; t < Taps<F>::N; ++t) {
+                const float wt = __fmul_rn(ax.w[t], ay.w[s]);
+                float T[C];
+                fetch_texel<KIND>(v, ax.base + t, ay.base + s, T);
+#pragma unroll
+                for (int c = 0; c < C; ++c) res[c] = fmaf(wt, T[c], res[c]);
+            }
+        }
+    } else {
+        // one-tap STF: one texel drawn from the lane's own filter PMF (Section 2.2, Section S1)
+        uint32_t ra = (uint32_t)x, rb = (uint32_t)y, rc = v.rng_z, rd = v.rng_w;
+        pcg4d(ra, rb, rc, rd);
+        const float ux = __uint2float_rn(ra >> 8) * (1.0f / 16777216.0f);
+        const float uy = __uint2float_rn(rb >> 8) * (1.0f / 16777216.0f);
+        Axis<F> ax, ay;
+        axis_select<F>(cx, ux, ax);
+        axis_select<F>(cy, uy, ay);
+        const float p = __fmul_rn(ax.p, ay.p);
+        float T[C];
+        fetch_texel<KIND>(v, ax.n, ay.n, T);
+        pk = pack_idx(ax.n, ay.n);
+        if constexpr (MODE == 1) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) res[c] = T[c];
+        } else {
+            // sharing over the lane's footprint with w_j = f_c(x_j) / f_j(x_j) (Eq. estimator-
+            // for-stf, Section 4.5 listing); the own lane's weight is exactly 1, texels outside
+            // the own filter weigh 0.
+            using FP = Footprint<MODE, TW, TH>;
+            const float rinv = fminf(__frcp_rn(p), FLT_MAX);
+            const int b0 = FP::base(lx, ly);
+            float acc[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+            float wsum = 0.0f;
+#pragma unroll
+            for (int r = 0; r < FP::KY; ++r) {
+#pragma unroll
+                for (int q = 0; q < FP::KX; ++q) {
+                    const int src = b0 + r * TW + q;
+                    const uint32_t pkj = __shfl_sync(kFull, pk, src);
+                    const float rj = __shfl_sync(kFull, rinv, src);
+                    const float pc = axis_weight_of<F>(ax, unpack_x(pkj)) * axis_weight_of<F>(ay, unpack_y(pkj));
+                    const float wt = (src == lane) ? 1.0f : pc * rj;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[c] = fmaf(wt, __shfl_sync(kFull, T[c], src), acc[c]);
+                    wsum += wt;
+                }
+            }
+            const float inv = __frcp_rn(wsum);
+#pragma unroll
+            for (int c = 0; c < C; ++c) res[c] = acc[c] * inv;
+        }
+    }
+
+    if (x < v.width && y < v.height) {
+        const float4 o = finish_pixel<C>(v, res, u, w);
+        __stcs(reinterpret_cast<float4*>(v.out + (size_t)y * v.pitch + 4 * (size_t)x), o);
+        const size_t pix = (size_t)y * v.width + x;
+        if (v.dbg_idx) v.dbg_idx[pix] = pk;
+        if (v.dbg_ch) {
+            float4* d = reinterpret_cast<float4*>(v.dbg_ch + pix * 8);
+            float z[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) z[c] = (c < C && c < v.c_true) ? res[c < C ? c : 0] : 0.0f;
+            d[0] = make_float4(z[0], z[1], z[2], z[3]);
+            d[1] = make_float4(z[4], z[5], z[6], z[7]);
+        }
+    }
+}
+
+constexpr int kWarpsPerBlock = 8;
+
+// One view: warp (block * 8 + warp) renders tile number t in row-major tile order.
+template <int KIND, int F, int MODE, int TW, int TH>
+__global__ void __launch_bounds__(256) k_render_view(const DevView v)
+{
+    const int t = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (t >= v.tiles_x * v.tiles_y) return;  // warp-uniform
+    const int ty = t / v.tiles_x;
+    const int tx = t - ty * v.tiles_x;
+    render_tile<KIND, F, MODE, TW, TH>(v, tx, ty, threadIdx.x & 31);
+}
+
+}  // namespace stf

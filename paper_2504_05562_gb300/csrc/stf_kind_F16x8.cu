@@ -1,0 +1,3 @@
+// Render kernels for material kind K_F16x8.
+#include "stf_launch.cuh"
+STF_INSTANTIATE_KIND(stf::K_F16x8, launch_view_F16x8)

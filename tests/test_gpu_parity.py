@@ -1,0 +1,160 @@
+"""GPU path vs the CPU oracle, element by element, through the C-ABI.
+
+Selected texel indices must match bit for bit; filtered channels and output colours within
+|a - b| <= 1e-5 * max(|b|, 1e-3) (FP32 colours; the GPU may fuse multiply-adds and use
+reciprocals in the colour path, the selection path is rounded identically on both sides).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_05562_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+def _stf():
+    from paper_2504_05562_gb300 import stf
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return stf
+
+
+def assert_close(gpu, ref, what):
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    bad = ~(np.abs(gpu - ref) <= RTOL * np.maximum(np.abs(ref), 1e-3))
+    if bad.any():
+        i = np.argwhere(bad)[0]
+        raise AssertionError("%s: %d mismatches, first at %s gpu=%r ref=%r" %
+                             (what, int(bad.sum()), tuple(i), gpu[tuple(i)], ref[tuple(i)]))
+
+
+def run_both(mat, view, mode, seed, tex=None):
+    stf = _stf()
+    tex = tex or stf.Texture(mat)
+    out, idx, ch = stf.render(tex, view, mode, seed=seed, debug=True)
+    torch.cuda.synchronize()
+    stf.sync()
+    r_out, r_idx, r_ch = O.render(mat, view, mode, seed=seed, want_channels=True)
+    g_idx = idx.cpu().numpy().view(np.uint32)
+    if mode != O.FULL:
+        mism = g_idx != r_idx
+        assert not mism.any(), "index mismatch at %s: gpu %x ref %x" % (
+            tuple(np.argwhere(mism)[0]), g_idx[mism][0], r_idx[mism][0])
+    assert_close(ch.cpu().numpy(), r_ch, "channels")
+    assert_close(out.cpu().numpy(), r_out, "rgba")
+    return out, r_out
+
+
+MODES = [O.FULL, O.ONE_TAP, O.QUAD2, O.WAVE2, O.WAVE3, O.WAVE4]
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("mode", MODES)
+def test_config1_all_modes(filt, mode):
+    mat = W.material_c1()
+    run_both(mat, W.config1_view(filt), mode, seed=0)
+
+
+@pytest.mark.parametrize("tile", [(8, 4), (4, 8), (16, 2)])
+@pytest.mark.parametrize("mode", [O.QUAD2, O.WAVE2, O.WAVE3, O.WAVE4])
+def test_tiles_ragged_screen(tile, mode):
+    """250 x 123 pixels: partial tiles on the right and bottom edges, several tile shapes."""
+    mat = W.material_c1()
+    for filt in (0, 1):
+        v = W.screen_aligned_view(250, 123, 64, 64, 3.3, filt, origin=(5.2, 7.9), tile=tile, frame=3)
+        run_both(mat, v, mode, seed=12345)
+
+
+def test_seed_frame_view_streams():
+    mat = W.material_c1()
+    v = W.config1_view(1)
+    v.update(frame=65535, view_id=4095)
+    run_both(mat, v, O.WAVE3, seed=(1 << 63) + 987654321)
+
+
+@pytest.mark.parametrize("mode", [O.FULL, O.ONE_TAP, O.QUAD2, O.WAVE3])
+def test_config2_reduced_shaded(mode):
+    mat = W.material_c2(size=256)
+    v = W.config2_view(width=320, height=180, tex=256, frame=2)
+    run_both(mat, v, mode, seed=7)
+
+
+@pytest.mark.parametrize("fmt", [W.FP32, W.FP16, W.BF16, W.E4M3])
+@pytest.mark.parametrize("filt,mode", [(0, O.QUAD2), (1, O.WAVE3), (1, O.FULL)])
+def test_config3_formats_reduced(fmt, filt, mode):
+    mat = W.material_c3(fmt, size=512)
+    v = W.config3_view(filt, width=480, height=272, tex=512)
+    run_both(mat, v, mode, seed=3)
+
+
+def test_widened_materials():
+    """Plane combinations without a dedicated kernel are widened to FP32 at creation."""
+    src = W.brick_material(128)
+    mats = [W.make_material(src[..., :3], W.FP16),                         # 3 x FP16
+            W.make_material(src[..., :6], W.UNORM8),                       # 6 x UNORM8
+            W.make_material(src, W.BF16) | {"scales": np.full((2, 2, 8), 0.5, np.float32),
+                                            "scale_tile": 64},             # scaled BF16
+            {"width": 128, "height": 128, "planes": [(W.FP32, 1, src[..., 0].astype(np.float32)),
+                                                      (W.E4M3, 2, W.encode_e4m3(src[..., 1:3]))],
+             "scales": None, "scale_tile": 0}]
+    for m in mats:
+        v = W.screen_aligned_view(96, 64, 128, 128, 2.5, 1, origin=(3.0, 4.0))
+        run_both(m, v, O.WAVE3, seed=5)
+
+
+def test_edge_cases():
+    mat = W.material_c1()
+    stf = _stf()
+    tex = stf.Texture(mat)
+    # a single pixel, a single row, minification, extreme magnification, uv outside [0, 1]
+    views = [W.screen_aligned_view(1, 1, 64, 64, 4.0, 0),
+             W.screen_aligned_view(77, 1, 64, 64, 2.0, 1),
+             W.screen_aligned_view(64, 64, 64, 64, 0.3, 1),
+             W.screen_aligned_view(64, 64, 64, 64, 64.0, 0, origin=(31.6, 31.2)),
+             W.screen_aligned_view(64, 64, 64, 64, 1.0, 1, origin=(-20.0, 30.0))]
+    for v in views:
+        for mode in MODES:
+            run_both(mat, v, mode, seed=99, tex=tex)
+
+
+def test_minification_reuse_equals_one_tap_bitwise():
+    stf = _stf()
+    mat = W.material_c1()
+    tex = stf.Texture(mat)
+    v = W.screen_aligned_view(64, 64, 64, 64, 0.24, 1, origin=(1.0, 2.0))
+    base, _, _ = stf.render(tex, v, O.ONE_TAP, seed=4)
+    for mode in (O.QUAD2, O.WAVE2, O.WAVE3, O.WAVE4):
+        got, _, _ = stf.render(tex, v, mode, seed=4)
+        assert torch.equal(got, base)
+
+
+def test_pitched_output_and_other_pixels_untouched():
+    stf = _stf()
+    mat = W.material_c1()
+    tex = stf.Texture(mat)
+    v = W.config1_view(0)
+    big = torch.full((256, 300, 4), -7.0, device="cuda")
+    out = big[:, :256]
+    stf.render(tex, v, O.WAVE3, seed=1, out=out)
+    torch.cuda.synchronize()
+    assert torch.all(big[:, 256:] == -7.0)
+    r_out, _, _ = O.render(mat, v, O.WAVE3, seed=1)
+    assert_close(out.cpu().numpy(), r_out, "pitched rgba")
+
+
+def test_full_size_config2_frame():
+    """1920 x 1080 B-spline 3x3 sharing with shading, the bench's launch configuration."""
+    mat = W.material_c2()
+    v = W.config2_view(frame=5)
+    run_both(mat, v, O.WAVE3, seed=0)
+
+
+def test_full_size_config3_fp16_frame():
+    mat = W.material_c3(W.FP16)
+    v = W.config3_view(1, frame=1)
+    run_both(mat, v, O.WAVE3, seed=0)
