@@ -99,6 +99,8 @@ def lib():
             L.stf_ref_render_exact_f64.argtypes = [C.POINTER(RefMaterial), C.POINTER(RefView), C.c_void_p,
                                                    C.c_void_p, C.c_int]
             L.stf_ref_render_exact_f64.restype = C.c_int
+            L.stf_ref_shade_sensitivity.argtypes = [C.POINTER(RefView), C.c_int, C.c_void_p, C.c_void_p, C.c_int]
+            L.stf_ref_shade_sensitivity.restype = C.c_int
             L.stf_ref_fetch_texel.argtypes = [C.POINTER(RefMaterial), C.c_int, C.c_int, C.POINTER(C.c_float)]
             _bind_neural(L)
             _lib = L
@@ -268,6 +270,16 @@ def render_exact_f64(mat, view, nthreads=None, want_channels=False):
         raise ValueError("oracle exact render rejected its arguments (rc=%d)" % rc)
     del keep
     return out, ch
+
+
+def shade_sensitivity(view, channels, nchannels):
+    """sum_k |d rgb / d ch_k| * max(|ch_k|, 1) per pixel, float64 [h, w, 3]."""
+    v = _view_struct(view)
+    ch = np.ascontiguousarray(channels, np.float32)
+    h, w = ch.shape[:2]
+    out = np.zeros((h, w, 3), np.float64)
+    lib().stf_ref_shade_sensitivity(C.byref(v), nchannels, ch.ctypes.data, out.ctypes.data, h * w)
+    return out
 
 
 def unpack_idx(idx):

@@ -397,6 +397,43 @@ void stf_ref_shade_f64(const ref_view* v, const double* ch, double u, double vv,
     for (int c = 0; c < 3; ++c) rgba[c] = ao * NL * (alb[c] + ORACLE_PI_D * spec);
 }
 
+/* Condition of shading with respect to the filtered channels: for each pixel and colour
+ * channel, sum_k |d colour / d ch_k| * max(|ch_k|, 1) by central differences in FP64. Used by
+ * the tests to bound how far a few-ulp change of the filtered channels can move the shaded
+ * colour (the shading is ill-conditioned near the terminator and at grazing normals). */
+int stf_ref_shade_sensitivity(const ref_view* v, int C, const float* ch, double* sens, int npix)
+{
+    const float* H = v->H;
+    for (int i = 0; i < npix; ++i) {
+        int x = i % v->width, y = i / v->width;
+        float u, w;
+        {
+            float px = (float)x + 0.5f, py = (float)y + 0.5f;
+            float hx = H[0] * px + H[1] * py + H[2];
+            float hy = H[3] * px + H[4] * py + H[5];
+            float hw = H[6] * px + H[7] * py + H[8];
+            u = hx / hw;
+            w = hy / hw;
+        }
+        double base[REF_MAX_CH], a[4], b[4];
+        for (int c = 0; c < REF_MAX_CH; ++c) base[c] = ch[(size_t)i * REF_MAX_CH + c];
+        double acc[3] = {0, 0, 0};
+        for (int k = 0; k < C; ++k) {
+            double sc = fabs(base[k]) > 1.0 ? fabs(base[k]) : 1.0;
+            double h = 1e-7 * sc;
+            double save = base[k];
+            base[k] = save + h;
+            stf_ref_shade_f64(v, base, u, w, a);
+            base[k] = save - h;
+            stf_ref_shade_f64(v, base, u, w, b);
+            base[k] = save;
+            for (int c = 0; c < 3; ++c) acc[c] += fabs(a[c] - b[c]) / (2.0 * h) * sc;
+        }
+        for (int c = 0; c < 3; ++c) sens[(size_t)i * 3 + c] = acc[c];
+    }
+    return 0;
+}
+
 /* ---------------------------------------------------------- FP32 render */
 
 typedef struct {

@@ -78,6 +78,10 @@ void stf_ref_texel_coords(const ref_view* v, int tex_w, int tex_h, int x, int y,
 void stf_ref_shade(const ref_view* v, const float* ch, float u, float vv, float* rgba);
 void stf_ref_shade_f64(const ref_view* v, const double* ch, double u, double vv, double* rgba);
 
+/* Per pixel and colour channel: sum_k |d colour / d ch_k| * max(|ch_k|, 1) (FP64 central
+ * differences) at the given filtered channels ch [npix][8]; sens [npix][3]. */
+int stf_ref_shade_sensitivity(const ref_view* v, int C, const float* ch, double* sens, int npix);
+
 /* FP32 render of one view: out_rgba [h][w][4]; out_idx [h][w] packed (ix & 0xffff) | (iy << 16)
  * of the selected texel (one-tap and sharing modes), may be NULL; out_ch [h][w][8] filtered
  * channels before shading, may be NULL. Returns 0 on success. */

@@ -1,8 +1,17 @@
 """GPU path vs the CPU oracle, element by element, through the C-ABI.
 
-Selected texel indices must match bit for bit; filtered channels and output colours within
-|a - b| <= 1e-5 * max(|b|, 1e-3) (FP32 colours; the GPU may fuse multiply-adds and use
-reciprocals in the colour path, the selection path is rounded identically on both sides).
+Selected texel indices must match bit for bit. Filtered channels and output colours must agree
+within |a - b| <= 1e-5 * max(|b|, s), with s the channel's full scale (max |texel|): a weighted
+sum of signed texels can cancel, and its rounding error is relative to its terms.
+
+Shaded colours are a function of the filtered channels that is ill-conditioned at the terminator
+and for grazing normals (a 1-ulp change of a normal component can move a dark pixel by 1e-3
+relative). They are checked as |a - b| <= 1e-5 * max(|b|, 1e-3) + 2^-20 * K, where K is the
+oracle's FP64 sensitivity sum_k |d colour / d ch_k| * max(|ch_k|, 1): the colour may differ by
+what a 16-ulp change of the filtered channels explains, plus 1e-5 relative.
+
+The GPU may fuse multiply-adds and use reciprocals in the colour path; the selection path is
+rounded identically on both sides.
 """
 import numpy as np
 import pytest
@@ -16,6 +25,16 @@ pytestmark = pytest.mark.gpu
 RTOL = 1e-5
 
 
+def channel_scale(mat):
+    """Full scale of each filtered channel (max |texel|, at least 1e-3): a weighted sum of signed
+    texels can cancel to near zero, and its rounding error is relative to the terms, not the sum."""
+    ref = W.decoded_reference(mat)
+    s = np.maximum(np.abs(ref).reshape(-1, ref.shape[-1]).max(0), 1e-3)
+    out = np.full(8, 1e-3)
+    out[:len(s)] = s
+    return out
+
+
 def _stf():
     from paper_2504_05562_gb300 import stf
     if not torch.cuda.is_available():
@@ -23,14 +42,17 @@ def _stf():
     return stf
 
 
-def assert_close(gpu, ref, what):
+def assert_close(gpu, ref, what, scale=1e-3, extra=0.0):
+    """|gpu - ref| <= 1e-5 * max(|ref|, scale) + extra; scale and extra broadcast."""
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
-    bad = ~(np.abs(gpu - ref) <= RTOL * np.maximum(np.abs(ref), 1e-3))
+    tol = RTOL * np.maximum(np.abs(ref), scale) + extra
+    bad = ~(np.abs(gpu - ref) <= tol)
     if bad.any():
         i = np.argwhere(bad)[0]
-        raise AssertionError("%s: %d mismatches, first at %s gpu=%r ref=%r" %
-                             (what, int(bad.sum()), tuple(i), gpu[tuple(i)], ref[tuple(i)]))
+        worst = float(np.max(np.abs(gpu - ref) / tol))
+        raise AssertionError("%s: %d mismatches, first at %s gpu=%r ref=%r, worst error / tolerance %.3g" %
+                             (what, int(bad.sum()), tuple(i), gpu[tuple(i)], ref[tuple(i)], worst))
 
 
 def run_both(mat, view, mode, seed, tex=None):
@@ -45,8 +67,15 @@ def run_both(mat, view, mode, seed, tex=None):
         mism = g_idx != r_idx
         assert not mism.any(), "index mismatch at %s: gpu %x ref %x" % (
             tuple(np.argwhere(mism)[0]), g_idx[mism][0], r_idx[mism][0])
-    assert_close(ch.cpu().numpy(), r_ch, "channels")
-    assert_close(out.cpu().numpy(), r_out, "rgba")
+    sc = channel_scale(mat)
+    assert_close(ch.cpu().numpy(), r_ch, "channels", sc)
+    if view.get("shading"):
+        nch = sum(p[1] for p in mat["planes"])
+        sens = O.shade_sensitivity(view, r_ch, nch)
+        k = np.concatenate([sens, np.zeros(sens.shape[:2] + (1,))], -1)
+        assert_close(out.cpu().numpy(), r_out, "rgba", 1e-3, 2.0 ** -20 * k)
+    else:
+        assert_close(out.cpu().numpy(), r_out, "rgba", sc[:4])
     return out, r_out
 
 
@@ -144,7 +173,7 @@ def test_pitched_output_and_other_pixels_untouched():
     torch.cuda.synchronize()
     assert torch.all(big[:, 256:] == -7.0)
     r_out, _, _ = O.render(mat, v, O.WAVE3, seed=1)
-    assert_close(out.cpu().numpy(), r_out, "pitched rgba")
+    assert_close(out.cpu().numpy(), r_out, "pitched rgba", channel_scale(mat)[:4])
 
 
 def test_full_size_config2_frame():
@@ -154,7 +183,9 @@ def test_full_size_config2_frame():
     run_both(mat, v, O.WAVE3, seed=0)
 
 
-def test_full_size_config3_fp16_frame():
+@pytest.mark.parametrize("filt", [0, 1])
+def test_full_size_config3_fp16_frame(filt):
+    """3840 x 2160 over the 2048^2 FP16 material: the benchmark's workload and launch configuration."""
     mat = W.material_c3(W.FP16)
-    v = W.config3_view(1, frame=1)
+    v = W.config3_view(filt, frame=1)
     run_both(mat, v, O.WAVE3, seed=0)
