@@ -367,6 +367,7 @@ void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long lon
     d.ch_ao = v.ch_ao;
     d.c_true = t->channels;
     d.neural = t->decoder_params;
+    d.affine = (v.H[6] == 0.0f && v.H[7] == 0.0f && v.H[8] == 1.0f) ? 1 : 0;
     if (!v.shading) d.shade_layout = 0;
     else if (v.ch_albedo == 0 && v.ch_normal == 3 && v.ch_rough == 5 && v.ch_ao == 6) d.shade_layout = 1;
     else if (v.ch_albedo == 0 && v.ch_normal == 4 && v.ch_rough == -1 && v.ch_ao == -1) d.shade_layout = 2;

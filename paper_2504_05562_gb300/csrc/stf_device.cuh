@@ -60,8 +60,23 @@ struct DevView {
     int ch_albedo, ch_normal, ch_rough, ch_ao;
     int c_true;               // channels of the material (alpha default when < 4)
     int filter, tile_w, tile_h;
+    int affine;               // H[6] == H[7] == 0 and H[8] == 1: hw == 1 exactly, no division needed
     const void* neural;       // decoder parameters for K_NEURAL
 };
+
+// Single-instruction approximations for the colour path (never for the texel choice).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // ------------------------------------------------------------------------------ RNG
 
@@ -90,47 +105,63 @@ __device__ __forceinline__ float w_bilinear(float d)
     return fmaxf(__fsub_rn(1.0f, fabsf(d)), 0.0f);
 }
 
-// Uniform cubic B-spline per axis with a = |d|: ((3a - 6) a) a + 4 over 6 for a < 1,
-// (2 - a)^3 / 6 for a < 2, else 0; each step rounded once, "/ 6" as a multiply by the float
-// nearest 1/6.
-__device__ __forceinline__ float w_bspline(float d)
+// B-spline branches of W with a = |d|: r1 for a < 1, r2 for 1 <= a < 2 (each step rounded once).
+__device__ __forceinline__ float bspline_r1(float a)
 {
-    const float a = fabsf(d);
     float t = __fmul_rn(3.0f, a);
     t = __fsub_rn(t, 6.0f);
     t = __fmul_rn(t, a);
     t = __fmul_rn(t, a);
     t = __fadd_rn(t, 4.0f);
-    const float r1 = __fmul_rn(t, 1.0f / 6.0f);
+    return __fmul_rn(t, 1.0f / 6.0f);
+}
+__device__ __forceinline__ float bspline_r2(float a)
+{
     const float s = __fsub_rn(2.0f, a);
     float q = __fmul_rn(s, s);
     q = __fmul_rn(q, s);
-    const float r2 = __fmul_rn(q, 1.0f / 6.0f);
-    return a < 1.0f ? r1 : (a < 2.0f ? r2 : 0.0f);
+    return __fmul_rn(q, 1.0f / 6.0f);
 }
 
-template <int F> __device__ __forceinline__ float wfun(float d)
+// Weight of tap t (lattice point floor(c) + K0 + t, given as the exact float nf) of coordinate c.
+// For the B-spline the branch of W is known per tap: d = c - n lies in [1, 2] for t = 0, [0, 1]
+// for t = 1, [-1, 0] for t = 2 and [-2, -1] for t = 3 (c - floor(c) is in [0, 1] after
+// rounding). Where |d| lands exactly on 1 or 2 both candidate branches give the same float
+// (r1(1) = r2(1) = 1/6 in FP32, r2(2) = 0), so this equals W(c - n) bit for bit.
+template <int F> __device__ __forceinline__ float tap_weight(float c, float nf, int t)
 {
-    return F == 0 ? w_bilinear(d) : w_bspline(d);
+    const float d = __fsub_rn(c, nf);
+    if constexpr (F == 0) return w_bilinear(d);
+    const float a = fabsf(d);
+    return (t == 1 || t == 2) ? bspline_r1(a) : bspline_r2(a);
 }
 
 // One axis of a lane: its lattice base, the weights of its taps, and its one-tap selection.
 template <int F> struct Axis {
     int base;                  // floor(c) + K0: lattice index of tap 0
+    float basef;               // the same as a float (exact)
     float w[Taps<F>::N];       // W(c - (base + t))
     int n;                     // selected lattice index
+    float nf;                  // the same as a float
     float p;                   // its weight (the 1D PMF value)
 };
+
+// Tap weights only (for the deterministic filter).
+template <int F> __device__ __forceinline__ void axis_weights(float c, Axis<F>& A)
+{
+    const float i0f = floorf(c);
+    A.base = __float2int_rn(i0f) + Taps<F>::K0;
+    A.basef = __fadd_rn(i0f, (float)Taps<F>::K0);
+#pragma unroll
+    for (int t = 0; t < Taps<F>::N; ++t) A.w[t] = tap_weight<F>(c, __fadd_rn(A.basef, (float)t), t);
+}
 
 // Taps in increasing lattice order; running FP32 CDF; first tap with u < CDF, else the last
 // tap with positive weight.
 template <int F> __device__ __forceinline__ void axis_select(float c, float u, Axis<F>& A)
 {
     constexpr int NT = Taps<F>::N;
-    const int i0 = __float2int_rd(c);
-    A.base = i0 + Taps<F>::K0;
-#pragma unroll
-    for (int t = 0; t < NT; ++t) A.w[t] = wfun<F>(__fsub_rn(c, __int2float_rn(A.base + t)));
+    axis_weights<F>(c, A);
     float cdf = 0.0f;
     int pick = -1;
 #pragma unroll
@@ -145,28 +176,8 @@ template <int F> __device__ __forceinline__ void axis_select(float c, float u, A
 #pragma unroll
     for (int t = 1; t < NT; ++t) p = (pick == t) ? A.w[t] : p;
     A.n = A.base + pick;
+    A.nf = __fadd_rn(A.basef, __int2float_rn(pick));
     A.p = p;
-}
-
-// Tap weights only (for the deterministic filter).
-template <int F> __device__ __forceinline__ void axis_weights(float c, Axis<F>& A)
-{
-    const int i0 = __float2int_rd(c);
-    A.base = i0 + Taps<F>::K0;
-#pragma unroll
-    for (int t = 0; t < Taps<F>::N; ++t) A.w[t] = wfun<F>(__fsub_rn(c, __int2float_rn(A.base + t)));
-}
-
-// W(c - n) for another lane's lattice index n, read from this lane's tap weights: the taps are
-// the only lattice points with non-zero weight, and for them the value is the same rounded
-// expression as the selection used.
-template <int F> __device__ __forceinline__ float axis_weight_of(const Axis<F>& A, int n)
-{
-    const int k = n - A.base;
-    float r = 0.0f;
-#pragma unroll
-    for (int t = 0; t < Taps<F>::N; ++t) r = (k == t) ? A.w[t] : r;
-    return r;
 }
 
 // ------------------------------------------------------------------------------ coordinates
@@ -178,6 +189,11 @@ __device__ __forceinline__ void pixel_uv(const DevView& v, int x, int y, float& 
     const float py = __fadd_rn(__int2float_rn(y), 0.5f);
     const float hx = __fadd_rn(__fadd_rn(__fmul_rn(v.H[0], px), __fmul_rn(v.H[1], py)), v.H[2]);
     const float hy = __fadd_rn(__fadd_rn(__fmul_rn(v.H[3], px), __fmul_rn(v.H[4], py)), v.H[5]);
+    if (v.affine) {  // hw = 0 * px + 0 * py + 1 = 1 exactly, and x / 1 = x
+        u = hx;
+        w = hy;
+        return;
+    }
     const float hw = __fadd_rn(__fadd_rn(__fmul_rn(v.H[6], px), __fmul_rn(v.H[7], py)), v.H[8]);
     u = __fdiv_rn(hx, hw);
     w = __fdiv_rn(hy, hw);
@@ -298,44 +314,46 @@ template <> struct Mat<K_U8x4_F16x2> {
 
 // Lambert + GGX after filtering; see the interface header for the conventions. The GGX
 // denominator uses a^2 (N.H)^2 + |N x H|^2 (equal to (N.H)^2 (a^2 - 1) + 1 for unit vectors),
-// which keeps the specular peak well conditioned in FP32.
+// which keeps the specular peak well conditioned in FP32. With irradiance pi the specular term
+// pi * D * Vis * F simplifies to a^2 F / (2 t^2 (g_v + g_l)), t = the GGX denominator.
 __device__ __forceinline__ float4 shade(const DevView& v, float r0, float r1, float r2, float nx, float ny,
                                         float rough, float ao, float u, float w)
 {
-    const float z2 = 1.0f - nx * nx - ny * ny;
-    const float nz = sqrtf(fmaxf(z2, 0.0f));
-    const float inl = rsqrtf(nx * nx + nz * nz + ny * ny);
+    // tangent-space normal (X, Y, sqrt(1 - X^2 - Y^2)) has unit length unless |XY| > 1
+    const float xy2 = fmaf(nx, nx, ny * ny);
+    const float nz = sqrt_approx(fmaxf(1.0f - xy2, 0.0f));
+    const float inl = rsqrtf(fmaxf(xy2, 1.0f));
     const float N0 = nx * inl, N1 = nz * inl, N2 = ny * inl;  // world (x, y, z) = (T, N, B)
-    rough = fmaxf(rough, 0.02f);
-    const float P0 = v.p2w[0] * u + v.p2w[1] * w + v.p2w[2];
-    const float P2 = v.p2w[3] * u + v.p2w[4] * w + v.p2w[5];
+    const float P0 = fmaf(v.p2w[0], u, fmaf(v.p2w[1], w, v.p2w[2]));
+    const float P2 = fmaf(v.p2w[3], u, fmaf(v.p2w[4], w, v.p2w[5]));
     float V0 = v.cam[0] - P0, V1 = v.cam[1], V2 = v.cam[2] - P2;
-    const float ivl = rsqrtf(V0 * V0 + V1 * V1 + V2 * V2);
+    const float ivl = rsqrtf(fmaf(V0, V0, fmaf(V1, V1, V2 * V2)));
     V0 *= ivl; V1 *= ivl; V2 *= ivl;
     const float L0 = v.light[0], L1 = v.light[1], L2 = v.light[2];
-    const float NL = N0 * L0 + N1 * L1 + N2 * L2;
-    if (!(NL > 0.0f)) return make_float4(0.0f, 0.0f, 0.0f, 1.0f);
-    const float NV = fmaxf(N0 * V0 + N1 * V1 + N2 * V2, 1e-4f);
+    const float NL = fmaf(N0, L0, fmaf(N1, L1, N2 * L2));
+    const float NV = fmaxf(fmaf(N0, V0, fmaf(N1, V1, N2 * V2)), 1e-4f);
     float H0 = L0 + V0, H1 = L1 + V1, H2 = L2 + V2;
-    const float ihl = rsqrtf(H0 * H0 + H1 * H1 + H2 * H2);
+    const float ihl = rsqrtf(fmaf(H0, H0, fmaf(H1, H1, H2 * H2)));
     H0 *= ihl; H1 *= ihl; H2 *= ihl;
-    const float NH = fmaxf(N0 * H0 + N1 * H1 + N2 * H2, 0.0f);
-    const float VH = fmaxf(V0 * H0 + V1 * H1 + V2 * H2, 0.0f);
-    const float c0 = N1 * H2 - N2 * H1, c1 = N2 * H0 - N0 * H2, c2 = N0 * H1 - N1 * H0;
-    const float s2 = c0 * c0 + c1 * c1 + c2 * c2;
+    const float NH = fmaxf(fmaf(N0, H0, fmaf(N1, H1, N2 * H2)), 0.0f);
+    const float VH = fmaxf(fmaf(V0, H0, fmaf(V1, H1, V2 * H2)), 0.0f);
+    const float c0 = fmaf(N1, H2, -N2 * H1), c1 = fmaf(N2, H0, -N0 * H2), c2 = fmaf(N0, H1, -N1 * H0);
+    const float s2 = fmaf(c0, c0, fmaf(c1, c1, c2 * c2));
+    rough = fmaxf(rough, 0.02f);
     const float al = rough * rough;
     const float a2 = al * al;
-    const float t = a2 * NH * NH + s2;
-    const float D = a2 / (kPi * t * t);
-    const float gv = NL * sqrtf(NV * NV * (1.0f - a2) + a2);
-    const float gl = NV * sqrtf(NL * NL * (1.0f - a2) + a2);
-    const float Vis = 0.5f / (gv + gl);
+    const float t = fmaf(a2 * NH, NH, s2);
+    const float ia2 = 1.0f - a2;
+    const float NLp = fmaxf(NL, 0.0f);  // keeps g_v + g_l > 0 (and ps finite) when the pixel is unlit
+    const float gv = NLp * sqrt_approx(fmaf(NV * NV, ia2, a2));
+    const float gl = NV * sqrt_approx(fmaf(NLp * NLp, ia2, a2));
     const float q = 1.0f - VH;
     const float q2 = q * q;
-    const float F = 0.04f + 0.96f * (q2 * q2 * q);
-    const float ps = kPi * D * Vis * F;
-    const float k = ao * NL;
-    return make_float4(k * (r0 + ps), k * (r1 + ps), k * (r2 + ps), 1.0f);
+    const float F = fmaf(0.96f, q2 * q2 * q, 0.04f);
+    const float ps = __fdividef(0.5f * a2 * F, t * t * (gv + gl));
+    const float k = NL > 0.0f ? ao * NL : 0.0f;
+    const float kp = k * ps;
+    return make_float4(fmaf(k, r0, kp), fmaf(k, r1, kp), fmaf(k, r2, kp), 1.0f);
 }
 
 template <int C> __device__ __forceinline__ float pick_ch(const float (&f)[C], int idx)

@@ -30,7 +30,7 @@ __device__ __forceinline__ void fetch_texel(const DevView& v, int x, int y, floa
 // All 32 lanes execute every shuffle (off-screen lanes of a partial tile compute with
 // extrapolated coordinates and only skip the store).
 template <int KIND, int F, int MODE, int TW, int TH>
-__device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane)
+__device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane, float4* rec, float* wtab)
 {
     constexpr int C = Channels<KIND>::C;
     const int lx = lane % TW, ly = lane / TW;
@@ -79,31 +79,64 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
         } else {
             // sharing over the lane's footprint with w_j = f_c(x_j) / f_j(x_j) (Eq. estimator-
             // for-stf, Section 4.5 listing); the own lane's weight is exactly 1, texels outside
-            // the own filter weigh 0.
+            // the own filter weigh 0. Each lane publishes (texel coordinates, 1 / p, decoded texel)
+            // in its warp's shared-memory records; the footprint lanes' records are then read with
+            // 128-bit loads, the shared-memory form of WaveReadLaneAt.
             using FP = Footprint<MODE, TW, TH>;
-            const float rinv = fminf(__frcp_rn(p), FLT_MAX);
-            const int b0 = FP::base(lx, ly);
-            float acc[C];
+            static_assert(C % 2 == 0 && C <= 8, "channels are accumulated in pairs, at most 8");
+            // 1 / p_j once per owner; rcp.approx of a denormal p flushes to +inf, clamped so that a
+            // zero p_c still gives a zero weight
+            const float rinv = fminf(rcp_approx(p), FLT_MAX);
+            rec[3 * lane] = make_float4(ax.nf, ay.nf, rinv, __uint_as_float(pk));
+            rec[3 * lane + 1] = make_float4(T[0], T[1], C > 2 ? T[2 % C] : 0.0f, C > 3 ? T[3 % C] : 0.0f);
+            if constexpr (C > 4) rec[3 * lane + 2] = make_float4(T[4 % C], T[5 % C], T[6 % C], T[7 % C]);
+            if constexpr (F == 1) {
+                // this lane's tap weights, one column per lane (conflict-free indexed reads)
 #pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+                for (int t = 0; t < 4; ++t) { wtab[t * 32 + lane] = ax.w[t]; wtab[(4 + t) * 32 + lane] = ay.w[t]; }
+            }
+            __syncwarp();
+            const int b0 = FP::base(lx, ly);
+            float2 acc[C / 2];
+#pragma unroll
+            for (int c = 0; c < C / 2; ++c) acc[c] = make_float2(0.0f, 0.0f);
             float wsum = 0.0f;
 #pragma unroll
             for (int r = 0; r < FP::KY; ++r) {
 #pragma unroll
                 for (int q = 0; q < FP::KX; ++q) {
                     const int src = b0 + r * TW + q;
-                    const uint32_t pkj = __shfl_sync(kFull, pk, src);
-                    const float rj = __shfl_sync(kFull, rinv, src);
-                    const float pc = axis_weight_of<F>(ax, unpack_x(pkj)) * axis_weight_of<F>(ay, unpack_y(pkj));
-                    const float wt = (src == lane) ? 1.0f : pc * rj;
-#pragma unroll
-                    for (int c = 0; c < C; ++c) acc[c] = fmaf(wt, __shfl_sync(kFull, T[c], src), acc[c]);
+                    const float4 m = rec[3 * src];
+                    float wx, wy;
+                    if constexpr (F == 0) {  // W(c - n) evaluated as the oracle does
+                        wx = w_bilinear(__fsub_rn(cx, m.x));
+                        wy = w_bilinear(__fsub_rn(cy, m.y));
+                    } else {
+                        // the same values read from this lane's taps: lattice points outside the
+                        // taps have zero weight
+                        const uint32_t pj = __float_as_uint(m.w);
+                        const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
+                        const bool in = ((kx | ky) & ~3) == 0;
+                        wx = in ? wtab[kx * 32 + lane] : 0.0f;
+                        wy = in ? wtab[(4 + ky) * 32 + lane] : 0.0f;
+                    }
+                    const float wt = (src == lane) ? 1.0f : (wx * wy) * m.z;
+                    const float2 w2 = make_float2(wt, wt);
+                    const float4 t0 = rec[3 * src + 1];
+                    acc[0] = __ffma2_rn(w2, make_float2(t0.x, t0.y), acc[0]);
+                    if constexpr (C > 2) acc[1 % (C / 2)] = __ffma2_rn(w2, make_float2(t0.z, t0.w), acc[1 % (C / 2)]);
+                    if constexpr (C > 4) {
+                        const float4 t1 = rec[3 * src + 2];
+                        acc[2 % (C / 2)] = __ffma2_rn(w2, make_float2(t1.x, t1.y), acc[2 % (C / 2)]);
+                        acc[3 % (C / 2)] = __ffma2_rn(w2, make_float2(t1.z, t1.w), acc[3 % (C / 2)]);
+                    }
                     wsum += wt;
                 }
             }
-            const float inv = __frcp_rn(wsum);
+            __syncwarp();  // records are rewritten by the warp's next tile
+            const float inv = rcp_approx(wsum);
 #pragma unroll
-            for (int c = 0; c < C; ++c) res[c] = acc[c] * inv;
+            for (int c = 0; c < C / 2; ++c) { res[2 * c] = acc[c].x * inv; res[2 * c + 1] = acc[c].y * inv; }
         }
     }
 
@@ -125,15 +158,21 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
 
 constexpr int kWarpsPerBlock = 8;
 
-// One view: warp (block * 8 + warp) renders tile number t in row-major tile order.
+// Shared-memory sample records: 3 x 16 bytes per lane (texel coordinates and 1/p, then up to 8
+// decoded channels); the 48-byte stride keeps 128-bit reads of neighbouring lanes conflict-free.
+constexpr int kRecPerLane = 3;
+
+// One view: block (bx, by) holds 8 warps on tile row by, tiles bx * 8 .. bx * 8 + 7.
 template <int KIND, int F, int MODE, int TW, int TH>
 __global__ void __launch_bounds__(256) k_render_view(const DevView v)
 {
-    const int t = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (t >= v.tiles_x * v.tiles_y) return;  // warp-uniform
-    const int ty = t / v.tiles_x;
-    const int tx = t - ty * v.tiles_x;
-    render_tile<KIND, F, MODE, TW, TH>(v, tx, ty, threadIdx.x & 31);
+    __shared__ float4 recs[kWarpsPerBlock * 32 * kRecPerLane];
+    __shared__ float wtabs[kWarpsPerBlock * 32 * 8];
+    const int warp = threadIdx.x >> 5;
+    const int tx = blockIdx.x * kWarpsPerBlock + warp;
+    if (tx >= v.tiles_x) return;  // warp-uniform
+    render_tile<KIND, F, MODE, TW, TH>(v, tx, blockIdx.y, threadIdx.x & 31, recs + warp * 32 * kRecPerLane,
+                                       wtabs + warp * 32 * 8);
 }
 
 }  // namespace stf

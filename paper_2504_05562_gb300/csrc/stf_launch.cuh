@@ -12,9 +12,8 @@ namespace stf {
 template <int KIND, int F, int MODE, int TW, int TH>
 static cudaError_t launch_one(const DevView& v, cudaStream_t s)
 {
-    const long long tiles = (long long)v.tiles_x * v.tiles_y;
-    const unsigned grid = (unsigned)((tiles + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (grid == 0) return cudaSuccess;
+    const dim3 grid((unsigned)((v.tiles_x + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)v.tiles_y);
+    if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     k_render_view<KIND, F, MODE, TW, TH><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
     return cudaGetLastError();
 }
