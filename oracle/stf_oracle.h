@@ -6,8 +6,9 @@
  * TEST INFRASTRUCTURE ONLY. Nothing in the GPU library includes, links or calls
  * this code; only the test-suite, the smoke check and the benchmark's CPU-baseline
  * leg use it. It shares no source with the CUDA path: every definition here is
- * written out again from the paper (and, where the paper is silent, from the
- * readings listed in the design notes).
+ * written out again from the paper (and, where the paper is silent, from a stated
+ * reading: the cubic B-spline kernel, the pcg4d hash, clamp-to-edge addressing, the
+ * footprint placement and the shading model, each described where it is defined).
  *
  * Build: plain C99, -O2 -ffp-contract=off, so that every float expression is
  * evaluated as written (one IEEE rounding per operation, left to right).
