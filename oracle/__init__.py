@@ -55,6 +55,8 @@ class RefMaterial(C.Structure):
         ("plane_fmt", C.c_int * 4), ("plane_ch", C.c_int * 4),
         ("plane_data", C.c_void_p * 4),
         ("scales", C.c_void_p), ("scale_tile", C.c_int),
+        ("nn_lat16", C.c_void_p), ("nn_gw", C.c_int), ("nn_gh", C.c_int), ("nn_r", C.c_int),
+        ("nn_w16", C.c_void_p), ("nn_b32", C.c_void_p),
     ]
 
 
@@ -108,18 +110,106 @@ def lib():
 
 
 def _bind_neural(L):
-    if not hasattr(L, "stf_ref_mlp_forward"):
-        return
-    dp = C.c_void_p
-    L.stf_ref_neural_features.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_int, dp]
-    L.stf_ref_neural_features.restype = C.c_int
-    L.stf_ref_mlp_forward.argtypes = [dp, dp, C.c_int, dp, dp]
-    L.stf_ref_mlp_forward.restype = C.c_int
-    L.stf_ref_neural_decode.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_int, dp, dp, C.c_int, dp]
-    L.stf_ref_neural_decode.restype = C.c_int
-    L.stf_ref_neural_loss_grad.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, C.c_int, dp, C.c_int,
-                                           dp, dp, dp, dp]
+    dp, ci = C.c_void_p, C.c_int
+    L.stf_ref_neural_features.argtypes = [dp, ci, ci, ci, ci, dp]
+    L.stf_ref_neural_features.restype = ci
+    L.stf_ref_mlp_forward.argtypes = [dp, dp, ci, dp, dp]
+    L.stf_ref_mlp_forward.restype = ci
+    L.stf_ref_neural_decode.argtypes = [dp, ci, ci, ci, dp, ci, dp, dp, ci, dp]
+    L.stf_ref_neural_decode.restype = ci
+    L.stf_ref_neural_decode_f64.argtypes = [dp, ci, ci, ci, dp, dp, ci, dp]
+    L.stf_ref_neural_decode_f64.restype = ci
+    L.stf_ref_neural_loss_grad.argtypes = [dp, ci, ci, ci, dp, ci, dp, ci, dp, ci, dp, dp, dp]
     L.stf_ref_neural_loss_grad.restype = C.c_double
+    L.stf_ref_f16_round.argtypes = [C.c_float]
+    L.stf_ref_f16_round.restype = C.c_float
+    L.stf_ref_f32_to_f16.argtypes = [C.c_float]
+    L.stf_ref_f32_to_f16.restype = C.c_uint16
+
+
+NN_IN, NN_H, NN_OUT, NN_LAT = 24, 64, 8, 16
+NN_PARAMS = NN_H * NN_IN + NN_H + NN_H * NN_H + NN_H + NN_OUT * NN_H + NN_OUT
+
+
+def _p(a):
+    return a.ctypes.data
+
+
+def nn_split(P):
+    """Views (W1, b1, W2, b2, W3, b3) of a flat parameter vector."""
+    sizes = [NN_H * NN_IN, NN_H, NN_H * NN_H, NN_H, NN_OUT * NN_H, NN_OUT]
+    out, o = [], 0
+    for s in sizes:
+        out.append(P[o:o + s])
+        o += s
+    return out
+
+
+def nn_features(lat, R, ix, iy):
+    lat = np.ascontiguousarray(lat, np.float64)
+    gh, gw = lat.shape[:2]
+    x = np.zeros(NN_IN)
+    lib().stf_ref_neural_features(_p(lat), gw, gh, R, int(ix) | (int(iy) << 16), _p(x))
+    return x
+
+
+def nn_forward_f64(P, x):
+    P = np.ascontiguousarray(P, np.float64)
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, NN_IN)
+    y = np.zeros((x.shape[0], NN_OUT))
+    lib().stf_ref_mlp_forward(_p(P), _p(x), x.shape[0], _p(y), None)
+    return y
+
+
+def nn_loss_grad(lat, R, P, target, idx):
+    """FP64 loss and gradients (dP, dlat) over texel indices idx (packed ix | iy << 16)."""
+    lat = np.ascontiguousarray(lat, np.float64)
+    gh, gw = lat.shape[:2]
+    P = np.ascontiguousarray(P, np.float64)
+    t = np.ascontiguousarray(target, np.float32)
+    idx = np.ascontiguousarray(idx, np.int32)
+    dP = np.zeros(NN_PARAMS)
+    dl = np.zeros_like(lat)
+    loss = lib().stf_ref_neural_loss_grad(_p(lat), gw, gh, R, _p(P), NN_PARAMS, _p(t), t.shape[1], _p(idx),
+                                          idx.size, _p(dP), _p(dl), None)
+    return loss, dP, dl
+
+
+def nn_decode_f64(lat, R, P, idx):
+    lat = np.ascontiguousarray(lat, np.float64)
+    gh, gw = lat.shape[:2]
+    P = np.ascontiguousarray(P, np.float64)
+    idx = np.ascontiguousarray(idx, np.int32)
+    out = np.zeros((idx.size, NN_OUT))
+    lib().stf_ref_neural_decode_f64(_p(lat), gw, gh, R, _p(P), _p(idx), idx.size, _p(out))
+    return out
+
+
+def nn_pack_inference(lat, P):
+    """FP16 codes of the latent grid and of W1, W2, W3 (round to nearest even, numpy) and the
+    FP32 biases: the inference parameters both paths consume."""
+    W1, b1, W2, b2, W3, b3 = nn_split(np.asarray(P, np.float64))
+    lat16 = np.ascontiguousarray(np.asarray(lat, np.float32).astype(np.float16)).view(np.uint16)
+    w16 = np.concatenate([W1, W2, W3]).astype(np.float32).astype(np.float16).view(np.uint16)
+    b32 = np.concatenate([b1, b2, b3]).astype(np.float32)
+    return lat16, np.ascontiguousarray(w16), np.ascontiguousarray(b32)
+
+
+def nn_decode_f32(lat16, R, w16, b32, idx):
+    """FP32 emulation of the GPU inference precision (FP16 storage, FP32 accumulation)."""
+    lat16 = np.ascontiguousarray(lat16, np.uint16)
+    gh, gw = lat16.shape[:2]
+    idx = np.ascontiguousarray(idx, np.int32)
+    out = np.zeros((idx.size, NN_OUT), np.float32)
+    lib().stf_ref_neural_decode(_p(lat16), gw, gh, R, _p(w16), w16.size, _p(b32), _p(idx), idx.size, _p(out))
+    return out
+
+
+def neural_material(width, height, lat16, R, w16, b32):
+    """Material dict for a neural texture (the oracle decodes with the FP32 emulation)."""
+    return {"width": width, "height": height, "planes": [], "scales": None, "scale_tile": 0,
+            "neural": (np.ascontiguousarray(lat16, np.uint16), R, np.ascontiguousarray(w16, np.uint16),
+                       np.ascontiguousarray(b32, np.float32))}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -182,6 +272,12 @@ def _material_struct(mat):
     else:
         m.scales = None
         m.scale_tile = 0
+    nn = mat.get("neural")
+    if nn is not None:
+        lat16, R, w16, b32 = nn
+        keep.extend([lat16, w16, b32])
+        m.nn_lat16, m.nn_gh, m.nn_gw, m.nn_r = lat16.ctypes.data, lat16.shape[0], lat16.shape[1], int(R)
+        m.nn_w16, m.nn_b32 = w16.ctypes.data, b32.ctypes.data
     return m, keep
 
 

@@ -196,6 +196,7 @@ static int fmt_bytes(int fmt)
 
 static int material_channels(const ref_material* m)
 {
+    if (m->nn_lat16) return 8;
     int c = 0;
     for (int p = 0; p < m->num_planes; ++p) c += m->plane_ch[p];
     return c;
@@ -209,6 +210,11 @@ static void fetch_texel(const ref_material* m, int x, int y, float* out)
     if (x > m->width - 1) x = m->width - 1;
     if (y < 0) y = 0;
     if (y > m->height - 1) y = m->height - 1;
+    if (m->nn_lat16) {
+        int packed = x | (y << 16);
+        stf_ref_neural_decode(m->nn_lat16, m->nn_gw, m->nn_gh, m->nn_r, m->nn_w16, 0, m->nn_b32, &packed, 1, out);
+        return;
+    }
     int C = material_channels(m);
     int ch = 0;
     for (int p = 0; p < m->num_planes; ++p) {
@@ -542,7 +548,11 @@ static int check_args(const ref_material* m, const ref_view* v)
 {
     if (!m || !v) return 1;
     if (m->width < 1 || m->height < 1 || m->width > 16384 || m->height > 16384) return 1;
-    if (m->num_planes < 1 || m->num_planes > REF_MAX_PLANES) return 1;
+    if (m->nn_lat16) {
+        if (m->num_planes != 0 || m->nn_r < 1 || m->nn_gw < 1 || m->nn_gh < 1) return 1;
+    } else if (m->num_planes < 1 || m->num_planes > REF_MAX_PLANES) {
+        return 1;
+    }
     int C = material_channels(m);
     if (C < 1 || C > REF_MAX_CH) return 1;
     if (m->scales && m->scale_tile < 1) return 1;

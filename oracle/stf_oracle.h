@@ -42,7 +42,18 @@ typedef struct {
     const void* plane_data[REF_MAX_PLANES]; /* row-major, channels interleaved */
     const float* scales;           /* NULL, or [tiles_y][tiles_x][total channels] */
     int scale_tile;                /* tile edge in texels when scales != NULL */
+    /* Neural material (num_planes == 0): latent grid [nn_gh][nn_gw][16] binary16 codes, the
+     * binary16 codes of W1, W2, W3 and the FP32 biases b1, b2, b3 (see stf_oracle_neural.c);
+     * texels are decoded by the FP32 emulation of the GPU's inference precision. */
+    const uint16_t* nn_lat16;
+    int nn_gw, nn_gh, nn_r;
+    const uint16_t* nn_w16;
+    const float* nn_b32;
 } ref_material;
+
+/* Neural decoder (stf_oracle_neural.c). */
+int stf_ref_neural_decode(const uint16_t* lat16, int GW, int GH, int R, const uint16_t* w16, int nw,
+                          const float* b32, const int* idx, int n, float* out);
 
 typedef struct {
     int width, height;             /* pixels */

@@ -1,0 +1,311 @@
+/*
+ * CPU oracle for the neural texel decoder (latent grid + MLP) that stands in for the costly
+ * per-texel decode STF amortises (neural texture compression, Sections 1 and 5.7).
+ *
+ * TEST INFRASTRUCTURE ONLY (tests, smoke, benchmark CPU leg); shares no code with the GPU.
+ *
+ * The decoder of texel (ix, iy) of a W x H material with an R-times coarser latent grid
+ * (R = W / GW, 16 channels per latent cell):
+ *   latent position  l = (i + 0.5) / R - 0.5 per axis; bilinear over the grid, clamp-to-edge;
+ *   position phase   phi = ((i mod R) + 0.5) / R per axis; features sin/cos(2 pi phi),
+ *                    sin/cos(4 pi phi) for x then y;
+ *   input            x = (16 interpolated latents, 4 x-features, 4 y-features) (24 values);
+ *   MLP              h1 = relu(W1 x + b1) (64), h2 = relu(W2 h1 + b2) (64), y = W3 h2 + b3 (8).
+ * Parameter vector (FP32/FP64, this order): W1[64][24], b1[64], W2[64][64], b2[64], W3[8][64],
+ * b3[8] (6280 values). The loss of a batch is mean over texels and channels of (y - t)^2.
+ *
+ * Two evaluation paths:
+ *   FP64           forward and backward in double (gradient checks, ground truth);
+ *   FP32 emulation the GPU's inference precision: latents and weights stored in FP16, the 24
+ *                  inputs and both hidden layers rounded to FP16, products accumulated in FP32,
+ *                  biases and output in FP32.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#define NN_IN 24
+#define NN_H 64
+#define NN_OUT 8
+#define NN_LAT 16
+#define NN_PARAMS (NN_H * NN_IN + NN_H + NN_H * NN_H + NN_H + NN_OUT * NN_H + NN_OUT)
+
+static const double PI_D = 3.14159265358979323846;
+
+/* binary16 -> float (exact) and float -> binary16 round-to-nearest-even, from the IEEE 754
+ * definition (1 sign, 5 exponent bits biased by 15, 10 fraction bits). */
+static float h2f(uint16_t h)
+{
+    int s = (h >> 15) & 1, e = (h >> 10) & 31, f = h & 1023;
+    float r;
+    if (e == 0) r = ldexpf((float)f, -24);
+    else if (e == 31) r = f ? NAN : INFINITY;
+    else r = ldexpf((float)(1024 + f), e - 25);
+    return s ? -r : r;
+}
+
+static uint16_t f2h(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    uint16_t sign = (uint16_t)((u >> 16) & 0x8000u);
+    float a = fabsf(x);
+    if (isnan(x)) return (uint16_t)(sign | 0x7e00u);
+    if (a >= 65520.0f) return (uint16_t)(sign | 0x7c00u); /* rounds to infinity */
+    if (a < ldexpf(1.0f, -14)) {
+        /* subnormal: multiple of 2^-24, round to nearest even */
+        double q = (double)a * 16777216.0;
+        double fl = floor(q);
+        double r = q - fl;
+        uint32_t m = (uint32_t)fl;
+        if (r > 0.5 || (r == 0.5 && (m & 1u))) m++;
+        return (uint16_t)(sign | m); /* m == 1024 becomes the smallest normal, as it should */
+    }
+    int e;
+    double fr = frexp((double)a, &e); /* a = fr * 2^e, fr in [0.5, 1) */
+    double q = fr * 2048.0;           /* 11 significant bits */
+    double fl = floor(q);
+    double r = q - fl;
+    uint32_t m = (uint32_t)fl;
+    if (r > 0.5 || (r == 0.5 && (m & 1u))) m++;
+    if (m == 2048) { m = 1024; e++; }
+    int E = e - 1 + 15;
+    if (E >= 31) return (uint16_t)(sign | 0x7c00u);
+    return (uint16_t)(sign | (uint16_t)(E << 10) | (uint16_t)(m - 1024));
+}
+
+static float round_h(float x) { return h2f(f2h(x)); }
+
+float stf_ref_f16_round(float x) { return round_h(x); }
+uint16_t stf_ref_f32_to_f16(float x) { return f2h(x); }
+
+/* Bilinear position of texel i on the latent axis: lower cell and its fraction (exact dyadic for
+ * power-of-two R). */
+static void latent_axis(int i, int R, int G, int* c0, int* c1, double* f)
+{
+    double l = (i + 0.5) / R - 0.5;
+    double fl = floor(l);
+    *f = l - fl;
+    int a = (int)fl, b = a + 1;
+    if (a < 0) a = 0;
+    if (a > G - 1) a = G - 1;
+    if (b < 0) b = 0;
+    if (b > G - 1) b = G - 1;
+    *c0 = a;
+    *c1 = b;
+}
+
+static void phase_features(int i, int R, double* out4)
+{
+    double phi = ((i % R) + 0.5) / R;
+    out4[0] = sin(2.0 * PI_D * phi);
+    out4[1] = cos(2.0 * PI_D * phi);
+    out4[2] = sin(4.0 * PI_D * phi);
+    out4[3] = cos(4.0 * PI_D * phi);
+}
+
+/* The 24 inputs in FP64 from an FP64 latent grid [GH][GW][16]. */
+static void features_f64(const double* lat, int GW, int GH, int R, int ix, int iy, double* x)
+{
+    int x0, x1, y0, y1;
+    double fx, fy;
+    latent_axis(ix, R, GW, &x0, &x1, &fx);
+    latent_axis(iy, R, GH, &y0, &y1, &fy);
+    const double w[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+    const double* c[4] = {lat + ((size_t)y0 * GW + x0) * NN_LAT, lat + ((size_t)y0 * GW + x1) * NN_LAT,
+                          lat + ((size_t)y1 * GW + x0) * NN_LAT, lat + ((size_t)y1 * GW + x1) * NN_LAT};
+    for (int k = 0; k < NN_LAT; ++k) x[k] = w[0] * c[0][k] + w[1] * c[1][k] + w[2] * c[2][k] + w[3] * c[3][k];
+    phase_features(ix, R, x + 16);
+    phase_features(iy, R, x + 20);
+}
+
+/* Exported: FP64 inputs of texel (ix, iy) (test helper). Returns 0. */
+int stf_ref_neural_features(const double* lat, int GW, int GH, int R, int ix_iy, double* x)
+{
+    features_f64(lat, GW, GH, R, ix_iy & 0xffff, ix_iy >> 16, x);
+    return 0;
+}
+
+/* FP64 MLP forward of one input; keeps pre-activations for the backward pass. */
+static void mlp_f64(const double* P, const double* x, double* a1, double* a2, double* y)
+{
+    const double* W1 = P;
+    const double* b1 = W1 + NN_H * NN_IN;
+    const double* W2 = b1 + NN_H;
+    const double* b2 = W2 + NN_H * NN_H;
+    const double* W3 = b2 + NN_H;
+    const double* b3 = W3 + NN_OUT * NN_H;
+    double h1[NN_H], h2[NN_H];
+    for (int o = 0; o < NN_H; ++o) {
+        double s = b1[o];
+        for (int i = 0; i < NN_IN; ++i) s += W1[o * NN_IN + i] * x[i];
+        a1[o] = s;
+        h1[o] = s > 0 ? s : 0;
+    }
+    for (int o = 0; o < NN_H; ++o) {
+        double s = b2[o];
+        for (int i = 0; i < NN_H; ++i) s += W2[o * NN_H + i] * h1[i];
+        a2[o] = s;
+        h2[o] = s > 0 ? s : 0;
+    }
+    for (int o = 0; o < NN_OUT; ++o) {
+        double s = b3[o];
+        for (int i = 0; i < NN_H; ++i) s += W3[o * NN_H + i] * h2[i];
+        y[o] = s;
+    }
+}
+
+/* Exported: FP64 forward of n inputs x[n][24] with parameters P -> y[n][8]. */
+int stf_ref_mlp_forward(const double* P, const double* x, int n, double* y, double* unused)
+{
+    (void)unused;
+    double a1[NN_H], a2[NN_H];
+    for (int b = 0; b < n; ++b) mlp_f64(P, x + (size_t)b * NN_IN, a1, a2, y + (size_t)b * NN_OUT);
+    return 0;
+}
+
+/* FP64 loss and gradients over a batch of texels idx[n] (packed ix | iy << 16) of a target
+ * material tgt[H][W][8]: loss = mean over texels and channels of (y - t)^2. Writes dP[6280] and
+ * dlat[GH][GW][16] (both overwritten). Returns the loss. */
+double stf_ref_neural_loss_grad(const double* lat, int GW, int GH, int R, const double* P, int nparams,
+                                const float* tgt, int W, const int* idx, int n, double* dP, double* dlat,
+                                double* unused)
+{
+    (void)nparams;
+    (void)unused;
+    memset(dP, 0, sizeof(double) * NN_PARAMS);
+    memset(dlat, 0, sizeof(double) * (size_t)GW * GH * NN_LAT);
+    const double* W1 = P;
+    const double* W2 = W1 + NN_H * NN_IN + NN_H;
+    const double* W3 = W2 + NN_H * NN_H + NN_H;
+    double* dW1 = dP;
+    double* db1 = dW1 + NN_H * NN_IN;
+    double* dW2 = db1 + NN_H;
+    double* db2 = dW2 + NN_H * NN_H;
+    double* dW3 = db2 + NN_H;
+    double* db3 = dW3 + NN_OUT * NN_H;
+    double loss = 0.0;
+    const double scale = 1.0 / ((double)n * NN_OUT);
+    for (int b = 0; b < n; ++b) {
+        int ix = idx[b] & 0xffff, iy = idx[b] >> 16;
+        double x[NN_IN], a1[NN_H], a2[NN_H], y[NN_OUT], h1[NN_H], h2[NN_H];
+        features_f64(lat, GW, GH, R, ix, iy, x);
+        mlp_f64(P, x, a1, a2, y);
+        for (int o = 0; o < NN_H; ++o) { h1[o] = a1[o] > 0 ? a1[o] : 0; h2[o] = a2[o] > 0 ? a2[o] : 0; }
+        double g3[NN_OUT], g2[NN_H], g1[NN_H], gx[NN_IN];
+        const float* t = tgt + ((size_t)iy * W + ix) * NN_OUT;
+        for (int o = 0; o < NN_OUT; ++o) {
+            double d = y[o] - (double)t[o];
+            loss += d * d * scale;
+            g3[o] = 2.0 * d * scale;
+        }
+        for (int i = 0; i < NN_H; ++i) {
+            double s = 0;
+            for (int o = 0; o < NN_OUT; ++o) s += W3[o * NN_H + i] * g3[o];
+            g2[i] = a2[i] > 0 ? s : 0;
+        }
+        for (int i = 0; i < NN_H; ++i) {
+            double s = 0;
+            for (int o = 0; o < NN_H; ++o) s += W2[o * NN_H + i] * g2[o];
+            g1[i] = a1[i] > 0 ? s : 0;
+        }
+        for (int i = 0; i < NN_IN; ++i) {
+            double s = 0;
+            for (int o = 0; o < NN_H; ++o) s += W1[o * NN_IN + i] * g1[o];
+            gx[i] = s;
+        }
+        for (int o = 0; o < NN_OUT; ++o) {
+            db3[o] += g3[o];
+            for (int i = 0; i < NN_H; ++i) dW3[o * NN_H + i] += g3[o] * h2[i];
+        }
+        for (int o = 0; o < NN_H; ++o) {
+            db2[o] += g2[o];
+            for (int i = 0; i < NN_H; ++i) dW2[o * NN_H + i] += g2[o] * h1[i];
+            db1[o] += g1[o];
+            for (int i = 0; i < NN_IN; ++i) dW1[o * NN_IN + i] += g1[o] * x[i];
+        }
+        /* latent gradient: the bilinear weights route gx[0..15] to the four corners */
+        int x0, x1, y0, y1;
+        double fx, fy;
+        latent_axis(ix, R, GW, &x0, &x1, &fx);
+        latent_axis(iy, R, GH, &y0, &y1, &fy);
+        const double w[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+        const int cx[4] = {x0, x1, x0, x1}, cy[4] = {y0, y0, y1, y1};
+        for (int k = 0; k < 4; ++k)
+            for (int c = 0; c < NN_LAT; ++c) dlat[((size_t)cy[k] * GW + cx[k]) * NN_LAT + c] += w[k] * gx[c];
+    }
+    return loss;
+}
+
+/* FP32 emulation of the GPU inference precision. lat16 [GH][GW][16] binary16 codes; w16 the
+ * FP16 codes of W1, W2, W3 (in the parameter order, biases skipped); b32 the FP32 biases
+ * b1, b2, b3. Decodes n texels idx[n] -> out[n][8]. */
+int stf_ref_neural_decode(const uint16_t* lat16, int GW, int GH, int R, const uint16_t* w16, int nw,
+                          const float* b32, const int* idx, int n, float* out)
+{
+    (void)nw;
+    const uint16_t* W1 = w16;
+    const uint16_t* W2 = W1 + NN_H * NN_IN;
+    const uint16_t* W3 = W2 + NN_H * NN_H;
+    const float* b1 = b32;
+    const float* b2 = b1 + NN_H;
+    const float* b3 = b2 + NN_H;
+    for (int b = 0; b < n; ++b) {
+        int ix = idx[b] & 0xffff, iy = idx[b] >> 16;
+        int x0, x1, y0, y1;
+        double fxd, fyd;
+        latent_axis(ix, R, GW, &x0, &x1, &fxd);
+        latent_axis(iy, R, GH, &y0, &y1, &fyd);
+        const float fx = (float)fxd, fy = (float)fyd;
+        /* corner weights and the interpolation, rounded per operation in this order */
+        const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy);
+        const float w01 = (1.0f - fx) * fy, w11 = fx * fy;
+        const uint16_t* c00 = lat16 + ((size_t)y0 * GW + x0) * NN_LAT;
+        const uint16_t* c10 = lat16 + ((size_t)y0 * GW + x1) * NN_LAT;
+        const uint16_t* c01 = lat16 + ((size_t)y1 * GW + x0) * NN_LAT;
+        const uint16_t* c11 = lat16 + ((size_t)y1 * GW + x1) * NN_LAT;
+        float x[NN_IN];
+        for (int k = 0; k < NN_LAT; ++k) {
+            float s = w00 * h2f(c00[k]);
+            s = s + w10 * h2f(c10[k]);
+            s = s + w01 * h2f(c01[k]);
+            s = s + w11 * h2f(c11[k]);
+            x[k] = round_h(s);
+        }
+        double ph[8];
+        phase_features(ix, R, ph);
+        phase_features(iy, R, ph + 4);
+        for (int k = 0; k < 8; ++k) x[16 + k] = round_h((float)ph[k]);
+        float h1[NN_H], h2[NN_H];
+        for (int o = 0; o < NN_H; ++o) {
+            float s = 0.0f;
+            for (int i = 0; i < NN_IN; ++i) s = s + h2f(W1[o * NN_IN + i]) * x[i];
+            s = s + b1[o];
+            h1[o] = round_h(s > 0.0f ? s : 0.0f);
+        }
+        for (int o = 0; o < NN_H; ++o) {
+            float s = 0.0f;
+            for (int i = 0; i < NN_H; ++i) s = s + h2f(W2[o * NN_H + i]) * h1[i];
+            s = s + b2[o];
+            h2[o] = round_h(s > 0.0f ? s : 0.0f);
+        }
+        for (int o = 0; o < NN_OUT; ++o) {
+            float s = 0.0f;
+            for (int i = 0; i < NN_H; ++i) s = s + h2f(W3[o * NN_H + i]) * h2[i];
+            out[(size_t)b * NN_OUT + o] = s + b3[o];
+        }
+    }
+    return 0;
+}
+
+/* FP64 decode of n texels from an FP64 latent grid and parameters (no storage rounding). */
+int stf_ref_neural_decode_f64(const double* lat, int GW, int GH, int R, const double* P, const int* idx, int n,
+                              double* out)
+{
+    double x[NN_IN], a1[NN_H], a2[NN_H];
+    for (int b = 0; b < n; ++b) {
+        features_f64(lat, GW, GH, R, idx[b] & 0xffff, idx[b] >> 16, x);
+        mlp_f64(P, x, a1, a2, out + (size_t)b * NN_OUT);
+    }
+    return 0;
+}
