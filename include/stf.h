@@ -167,6 +167,54 @@ stf_status stf_sync(void);
 /* Message for the last non-OK status on the calling thread ("" if none). */
 const char* stf_last_error(void);
 
+/* ------------------------------------------------------------------------------------------
+ * Neural texel decoder (the costly per-texel decode that stochastic filtering amortises,
+ * Sections 1 and 5.7: neural texture compression). Not a model from the paper, whose
+ * compressed-material format is not given; this build's small stand-in:
+ *   latents: a latent_w x latent_h grid of 16 channels, R = tex_w / latent_w texels per cell
+ *            (a power of two <= 16, the same on both axes);
+ *   inputs:  the grid bilinearly interpolated at (i + 0.5) / R - 0.5 per axis (clamp-to-edge),
+ *            plus sin/cos(2 pi phi), sin/cos(4 pi phi) of phi = ((i mod R) + 0.5) / R per axis;
+ *   MLP:     24 -> 64 -> 64 -> 8 with ReLU; parameters W1[64][24], b1, W2[64][64], b2, W3[8][64],
+ *            b3 (6280 values, in this order).
+ * Training: Adam on the mean squared error over the 8 channels of an FP32 target texture,
+ * `batch` texels per step drawn by a counter hash of (step, seed); FP32 on the CUDA cores,
+ * bit-reproducible. Inference (render path, stf_decoder_decode): FP16 latents and weights, FP16
+ * inputs and hidden activations, FP32 accumulation on the tensor cores.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int tex_w, tex_h;
+    int latent_w, latent_h;
+    int batch;                     /* texels per step, a multiple of 256 */
+    float lr_latent, lr_mlp, beta1, beta2, eps;
+    unsigned long long seed;       /* initialisation and batch sampling */
+} stf_decoder_config;
+
+/* Creates a decoder with seeded random initialisation (device memory, library-owned). */
+stf_status stf_decoder_create(const stf_decoder_config* cfg, stf_decoder** out);
+/* Runs `steps` Adam steps against `target` (an 8-channel FP32 texture of the decoder's size);
+ * losses (host, may be NULL) receives each step's batch loss. Synchronous. */
+stf_status stf_decoder_train(stf_decoder* d, const stf_texture* target, int steps, float* losses);
+/* Loss and gradients over the given texels (host array of packed ix | iy << 16) without updating:
+ * grad_params (host, 6280), grad_latent (host, latent_w * latent_h * 16), loss (host). Synchronous. */
+stf_status stf_decoder_gradients(stf_decoder* d, const stf_texture* target, const int32_t* texels, int n,
+                                 float* grad_params, float* grad_latent, float* loss);
+/* Copies the FP32 parameters out (host) / in (host; the inference copy is refreshed). */
+stf_status stf_decoder_get_params(const stf_decoder* d, float* latent, float* params);
+stf_status stf_decoder_set_params(stf_decoder* d, const float* latent, const float* params);
+/* Decodes n texels (device array of packed ix | iy << 16) into out (device, n * 8 floats,
+ * 16-byte aligned) with the inference kernel. Asynchronous on the library stream. */
+stf_status stf_decoder_decode(const stf_decoder* d, const int32_t* texels, int n, float* out);
+/* Configuration and number of completed training steps. */
+stf_status stf_decoder_info(const stf_decoder* d, stf_decoder_config* cfg, long long* step);
+/* Checkpoints: parameters, Adam moments, step, configuration and a CRC-32 of the file. load
+ * rejects a wrong magic, an inconsistent header or a checksum mismatch with
+ * STF_ERR_INVALID_ARG before touching the GPU. */
+stf_status stf_decoder_save(const stf_decoder* d, const char* path);
+stf_status stf_decoder_load(const char* path, stf_decoder** out);
+/* Frees a decoder; textures created from it must be destroyed first. */
+stf_status stf_decoder_destroy(stf_decoder* d);
+
 /* Library version as major * 10000 + minor * 100 + patch. */
 int stf_version(void);
 

@@ -6,7 +6,7 @@
 #include <float.h>
 
 #include "stf_device.cuh"
-#include "stf_neural_device.cuh"
+#include "stf_neural.cuh"
 
 namespace stf {
 
@@ -18,19 +18,25 @@ template <> struct Channels<K_NEURAL> { static constexpr int C = 8; };
 // Fetch or decode one texel of lattice point (x, y) with clamp-to-edge addressing.
 // For K_NEURAL all 32 lanes must call it together (the decode is a warp-wide matrix product).
 template <int KIND>
-__device__ __forceinline__ void fetch_texel(const DevView& v, int x, int y, float (&t)[Channels<KIND>::C])
+__device__ __forceinline__ void fetch_texel(const DevView& v, int x, int y, float (&t)[Channels<KIND>::C],
+                                            unsigned char* scratch)
 {
     x = clampi(x, 0, v.tex_w - 1);
     y = clampi(y, 0, v.tex_h - 1);
-    if constexpr (KIND == K_NEURAL) neural_decode_warp(v, x, y, t);
+    if constexpr (KIND == K_NEURAL) nn_decode_warp(reinterpret_cast<const NeuralDev*>(v.neural), x, y, t, scratch);
     else Mat<KIND>::fetch(v, x, y, t);
 }
+
+// Per-warp shared scratch the texel decode needs (the neural decoder's A tile).
+template <int KIND> struct DecodeScratch { static constexpr int bytes = 16; };
+template <> struct DecodeScratch<K_NEURAL> { static constexpr int bytes = kNnWarpSmem; };
 
 // One warp tile of one view. MODE: 0 full filter, 1 one-tap, 2 quad 2x2, 3..5 wave k x k.
 // All 32 lanes execute every shuffle (off-screen lanes of a partial tile compute with
 // extrapolated coordinates and only skip the store).
 template <int KIND, int F, int MODE, int TW, int TH>
-__device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane, float4* rec, float* wtab)
+__device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane, float4* rec, float* wtab,
+                                            unsigned char* scratch)
 {
     constexpr int C = Channels<KIND>::C;
     const int lx = lane % TW, ly = lane / TW;
@@ -55,7 +61,7 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
             for (int t = 0; t < Taps<F>::N; ++t) {
                 const float wt = __fmul_rn(ax.w[t], ay.w[s]);
                 float T[C];
-                fetch_texel<KIND>(v, ax.base + t, ay.base + s, T);
+                fetch_texel<KIND>(v, ax.base + t, ay.base + s, T, scratch);
 #pragma unroll
                 for (int c = 0; c < C; ++c) res[c] = fmaf(wt, T[c], res[c]);
             }
@@ -71,7 +77,7 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
         axis_select<F>(cy, uy, ay);
         const float p = __fmul_rn(ax.p, ay.p);
         float T[C];
-        fetch_texel<KIND>(v, ax.n, ay.n, T);
+        fetch_texel<KIND>(v, ax.n, ay.n, T, scratch);
         pk = pack_idx(ax.n, ay.n);
         if constexpr (MODE == 1) {
 #pragma unroll
@@ -168,11 +174,12 @@ __global__ void __launch_bounds__(256) k_render_view(const DevView v)
 {
     __shared__ float4 recs[kWarpsPerBlock * 32 * kRecPerLane];
     __shared__ float wtabs[kWarpsPerBlock * 32 * 8];
+    __shared__ __align__(16) unsigned char scratch[kWarpsPerBlock * DecodeScratch<KIND>::bytes];
     const int warp = threadIdx.x >> 5;
     const int tx = blockIdx.x * kWarpsPerBlock + warp;
     if (tx >= v.tiles_x) return;  // warp-uniform
     render_tile<KIND, F, MODE, TW, TH>(v, tx, blockIdx.y, threadIdx.x & 31, recs + warp * 32 * kRecPerLane,
-                                       wtabs + warp * 32 * 8);
+                                       wtabs + warp * 32 * 8, scratch + warp * DecodeScratch<KIND>::bytes);
 }
 
 }  // namespace stf

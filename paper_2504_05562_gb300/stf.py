@@ -49,7 +49,9 @@ class View(C.Structure):
 _lock = threading.Lock()
 _lib = None
 EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_stream", "stf_sync",
-           "stf_last_error", "stf_version")
+           "stf_last_error", "stf_version", "stf_decoder_create", "stf_decoder_train", "stf_decoder_gradients",
+           "stf_decoder_get_params", "stf_decoder_set_params", "stf_decoder_decode", "stf_decoder_info",
+           "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy")
 
 
 def lib_path() -> str:
@@ -78,9 +80,8 @@ def load():
 
 
 def _bind_extra(L):
-    if hasattr(L, "stf_decoder_create"):
-        from . import neural
-        neural._bind(L)
+    from . import neural
+    neural._bind(L)
 
 
 def _check(status):

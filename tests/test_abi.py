@@ -61,3 +61,41 @@ def test_invalid_arguments_rejected_on_host():
     assert L.stf_create_texture(C.byref(d), C.byref(h)) == stf.ERR_INVALID_ARG
     assert h.value is None
     assert L.stf_destroy(None) == stf.OK
+
+
+def _ckpt_bytes(nlat=16 * 16 * 16, nparams=6280, crc_ok=True, magic=b"STFDEC01"):
+    import struct
+    import zlib
+    hdr = struct.pack("<8sI5i5f4xQqqii", magic, 1, 64, 64, 16, 16, 1024, 1e-2, 5e-3, 0.9, 0.99, 1e-10, 7, 10,
+                      nlat, nparams, 0)
+    assert len(hdr) == 88
+    payload = bytes(4 * (3 * nlat + 3 * nparams))
+    crc = zlib.crc32(hdr + payload)
+    if not crc_ok:
+        crc ^= 1
+    return hdr + payload + struct.pack("<I", crc)
+
+
+def test_corrupted_checkpoints_rejected_before_any_gpu_work(tmp_path):
+    """Checkpoint validation (magic, header consistency, CRC-32, length) happens on the host."""
+    from paper_2504_05562_gb300 import neural  # noqa: F401  (binds the decoder entry points)
+    L = stf.load()
+    h = C.c_void_p()
+    cases = {"bad_magic": _ckpt_bytes(magic=b"NOTADEC!"), "bad_crc": _ckpt_bytes(crc_ok=False),
+             "truncated": _ckpt_bytes()[:-100], "bad_header": _ckpt_bytes(nlat=5),
+             "trailing": _ckpt_bytes() + b"x"}
+    for name, data in cases.items():
+        p = tmp_path / (name + ".ckpt")
+        p.write_bytes(data)
+        assert L.stf_decoder_load(str(p).encode(), C.byref(h)) == stf.ERR_INVALID_ARG, name
+        assert h.value is None
+    assert "checksum" in (L.stf_decoder_load(str(tmp_path / "bad_crc.ckpt").encode(), C.byref(h)) and stf.last_error())
+    assert L.stf_decoder_load(str(tmp_path / "missing.ckpt").encode(), C.byref(h)) == stf.ERR_INVALID_ARG
+    # a well-formed file passes validation (its CRC-32 agrees with zlib's); without a GPU the load
+    # then stops at the first device allocation
+    p = tmp_path / "good.ckpt"
+    p.write_bytes(_ckpt_bytes())
+    rc = L.stf_decoder_load(str(p).encode(), C.byref(h))
+    assert rc != stf.ERR_INVALID_ARG, stf.last_error()
+    if rc == stf.OK:
+        L.stf_decoder_destroy(h)
