@@ -153,6 +153,35 @@ stf_status stf_create_texture(const stf_texture_desc* desc, stf_texture** out);
 stf_status stf_render_views(const stf_view* views, int n, int filter, int reuse_mode,
                             unsigned long long seed);
 
+/* Multi-view scheduling (used when stf_render_views gets n > 1 views). Views are grouped by
+ * material kind and cut into work items of 8 x schedule tiles; one persistent kernel per kind
+ * pulls items from a device counter, costliest views first. The view constants and item list go
+ * to the device in one copy from a pinned staging buffer; copy, counter reset and kernels are
+ * captured once into a CUDA graph and replayed while the batch keeps its shape (same views per
+ * kind, same item count). */
+enum { STF_OPT_BATCH_GRAPHS = 1 };                          /* 1 (default): replay CUDA graphs */
+enum { STF_STAT_GRAPH_BUILDS = 1, STF_STAT_GRAPH_REPLAYS = 2 };
+stf_status stf_set_option(int option, long long value);
+stf_status stf_get_stat(int stat, long long* value);
+
+/* Autotuner. A view class is (material kind, filter, estimator, magnification bucket at the view
+ * centre: <2, <8, <32, >=32 pixels per texel, resolution bucket: <0.5, <3, >=3 Mpixel). For
+ * every class present in `views`, stf_autotune renders the class's largest view with each warp
+ * tile (8x4, 4x8, 16x2; sharing modes only) and schedule (1, 2, 4, 8 tiles per warp per work
+ * item), times them with CUDA events on the library stream, and keeps the fastest. Views with
+ * tile 0x0 then use their class's tile; the schedule applies to multi-view batches. The tile
+ * shape changes the sharing footprints, so it changes the estimate (not its validity).
+ * Autotuning renders into the given views' outputs. Synchronous. */
+stf_status stf_autotune(const stf_view* views, int n, int filter, int reuse_mode, unsigned long long seed);
+/* Tile shape and schedule `view` would be rendered with. */
+stf_status stf_view_config(const stf_view* view, int filter, int reuse_mode, int* tile_w, int* tile_h,
+                           int* schedule);
+/* Text table of tuned classes (one "class tile_w tile_h schedule ms" line each, under a header
+ * naming the GPU); load merges entries into the current table. */
+stf_status stf_autotune_save(const char* path);
+stf_status stf_autotune_load(const char* path);
+stf_status stf_autotune_clear(void);
+
 /* Frees a texture (NULL is a no-op). The caller ensures no enqueued work still reads it. */
 stf_status stf_destroy(stf_texture* tex);
 

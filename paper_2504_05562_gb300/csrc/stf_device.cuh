@@ -21,6 +21,7 @@ constexpr float kCoordLo = -16384.0f;  // texel coordinates are clamped to [lo, 
 constexpr float kCoordHi = 32000.0f;
 constexpr float kPi = 3.14159265f;
 constexpr int kMaxCh = 8;
+constexpr int kWarpsPerBlock = 8;  // warps (pixel tiles in flight) per render block
 
 // Material kinds with a dedicated kernel. Anything else is widened to FP32 at creation.
 enum MatKind : int {
@@ -62,6 +63,12 @@ struct DevView {
     int filter, tile_w, tile_h;
     int affine;               // H[6] == H[7] == 0 and H[8] == 1: hw == 1 exactly, no division needed
     const void* neural;       // decoder parameters for K_NEURAL
+};
+
+// A run of tiles of one view for the persistent multi-view kernel. variant = filter * 3 + tile
+// shape (0: 8x4, 1: 4x8, 2: 16x2).
+struct WorkItem {
+    int view, tile0, ntiles, variant;
 };
 
 // Single-instruction approximations for the colour path (never for the texel choice).

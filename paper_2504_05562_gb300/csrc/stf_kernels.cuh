@@ -55,7 +55,9 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
         axis_weights<F>(cy, ay);
 #pragma unroll
         for (int c = 0; c < C; ++c) res[c] = 0.0f;
-#pragma unroll
+        // a neural decode is a warp-wide tensor-core product: keep one row of taps in flight
+        constexpr int kRowUnroll = KIND == K_NEURAL ? 1 : Taps<F>::N;
+#pragma unroll kRowUnroll
         for (int s = 0; s < Taps<F>::N; ++s) {
 #pragma unroll
             for (int t = 0; t < Taps<F>::N; ++t) {
@@ -162,15 +164,19 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
     }
 }
 
-constexpr int kWarpsPerBlock = 8;
 
 // Shared-memory sample records: 3 x 16 bytes per lane (texel coordinates and 1/p, then up to 8
 // decoded channels); the 48-byte stride keeps 128-bit reads of neighbouring lanes conflict-free.
 constexpr int kRecPerLane = 3;
 
+// Blocks resident per SM the kernel is compiled for: the neural decode is register-heavy and
+// needs at least two 8-warp blocks per SM to hide the tensor-core latency.
+template <int KIND> struct MinBlocks { static constexpr int n = 1; };
+template <> struct MinBlocks<K_NEURAL> { static constexpr int n = 2; };
+
 // One view: block (bx, by) holds 8 warps on tile row by, tiles bx * 8 .. bx * 8 + 7.
 template <int KIND, int F, int MODE, int TW, int TH>
-__global__ void __launch_bounds__(256) k_render_view(const DevView v)
+__global__ void __launch_bounds__(256, MinBlocks<KIND>::n) k_render_view(const DevView v)
 {
     __shared__ float4 recs[kWarpsPerBlock * 32 * kRecPerLane];
     __shared__ float wtabs[kWarpsPerBlock * 32 * 8];

@@ -51,7 +51,10 @@ _lib = None
 EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_stream", "stf_sync",
            "stf_last_error", "stf_version", "stf_decoder_create", "stf_decoder_train", "stf_decoder_gradients",
            "stf_decoder_get_params", "stf_decoder_set_params", "stf_decoder_decode", "stf_decoder_info",
-           "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy")
+           "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy", "stf_set_option", "stf_get_stat",
+           "stf_autotune", "stf_view_config", "stf_autotune_save", "stf_autotune_load", "stf_autotune_clear")
+OPT_BATCH_GRAPHS = 1
+STAT_GRAPH_BUILDS, STAT_GRAPH_REPLAYS = 1, 2
 
 
 def lib_path() -> str:
@@ -82,6 +85,17 @@ def load():
 def _bind_extra(L):
     from . import neural
     neural._bind(L)
+    L.stf_set_option.argtypes = [C.c_int, C.c_longlong]
+    L.stf_get_stat.argtypes = [C.c_int, C.POINTER(C.c_longlong)]
+    L.stf_autotune.argtypes = [C.POINTER(View), C.c_int, C.c_int, C.c_int, C.c_ulonglong]
+    L.stf_view_config.argtypes = [C.POINTER(View), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int)]
+    L.stf_autotune_save.argtypes = [C.c_char_p]
+    L.stf_autotune_load.argtypes = [C.c_char_p]
+    L.stf_autotune_clear.argtypes = []
+    for n in ("stf_set_option", "stf_get_stat", "stf_autotune", "stf_view_config", "stf_autotune_save",
+              "stf_autotune_load", "stf_autotune_clear"):
+        getattr(L, n).restype = C.c_int
 
 
 def _check(status):
@@ -217,3 +231,38 @@ def render(tex: Texture, view: dict, mode, seed=0, debug=False, out=None, filter
     ch = torch.zeros((h, w, 8), dtype=torch.float32, device="cuda") if debug else None
     render_views([make_view(view, tex, out, idx, ch)], filter, mode, seed)
     return out, idx, ch
+
+
+# ----------------------------------------------------------------------------- scheduling
+
+def set_option(option, value):
+    _check(load().stf_set_option(int(option), int(value)))
+
+
+def get_stat(stat):
+    v = C.c_longlong()
+    _check(load().stf_get_stat(int(stat), C.byref(v)))
+    return v.value
+
+
+def autotune(views, filter=FILTER_PER_VIEW, mode=MODE_WAVE3, seed=0):
+    arr = (View * len(views))(*views)
+    _check(load().stf_autotune(arr, len(views), int(filter), int(mode), int(seed) & (2 ** 64 - 1)))
+
+
+def view_config(view, filter=FILTER_PER_VIEW, mode=MODE_WAVE3):
+    tw, th, sc = C.c_int(), C.c_int(), C.c_int()
+    _check(load().stf_view_config(C.byref(view), int(filter), int(mode), C.byref(tw), C.byref(th), C.byref(sc)))
+    return tw.value, th.value, sc.value
+
+
+def autotune_save(path):
+    _check(load().stf_autotune_save(str(path).encode()))
+
+
+def autotune_load(path):
+    _check(load().stf_autotune_load(str(path).encode()))
+
+
+def autotune_clear():
+    _check(load().stf_autotune_clear())

@@ -40,9 +40,10 @@ def _all_texels(w, h):
 # Inference tolerance. Both sides round the same 24 FP16 inputs; they sum FP32 products in a
 # different order (tensor cores), so a hidden activation that lands within a few FP32 ulps of an
 # FP16 rounding boundary may round to the neighbouring FP16 value (2^-11 relative), which the
-# following layers carry to the output. Most outputs agree to FP32 rounding; a small fraction
-# carries one or more such flips.
-def assert_neural_close(gpu, ref, what):
+# following layers carry to the output. Most outputs agree to FP32 rounding; a small fraction of
+# decodes (about 1 in 200 here) carries such a flip, and a shared-sample estimate combines up to
+# 16 decodes, so the fraction of pixels that may exceed 1e-5 grows with the footprint.
+def assert_neural_close(gpu, ref, what, frac=0.02):
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
     err = np.abs(gpu - ref) / (1.0 + np.abs(ref))
@@ -50,7 +51,7 @@ def assert_neural_close(gpu, ref, what):
     info = "%s: max %.3g, median %.3g, fraction above 1e-5 %.4f" % (what, err.max(), np.median(err), frac_tight)
     assert err.max() <= 1e-2, info
     assert np.median(err) <= 1e-6, info
-    assert frac_tight <= 0.02, info
+    assert frac_tight <= frac, info
 
 
 def test_decode_matches_oracle_emulation():
@@ -130,7 +131,7 @@ def test_render_neural_material_parity():
         r_out, r_idx, r_ch = O.render(mat, v, mode, seed=2, want_channels=True)
         if mode != O.FULL:
             assert np.array_equal(idx.cpu().numpy().view(np.uint32), r_idx)
-        assert_neural_close(ch.cpu().numpy(), r_ch, "render channels mode %d" % mode)
+        assert_neural_close(ch.cpu().numpy(), r_ch, "render channels mode %d" % mode, frac=0.08)
 
 
 def test_checkpoint_resume_is_bit_exact(tmp_path):
