@@ -182,6 +182,25 @@ stf_status stf_autotune_save(const char* path);
 stf_status stf_autotune_load(const char* path);
 stf_status stf_autotune_clear(void);
 
+/* Allocation-free multi-view rendering (this entry point has no counterpart in the paper).
+ * For callers that cannot let a library allocate device memory: a render thread working inside a
+ * fixed, pre-reserved device-memory budget, or a frame loop that must not stall, since
+ * cudaMalloc / cudaFree can synchronise the device and can fail mid-frame. Renders the batch
+ * exactly as stf_render_views does (same kernels, same pixels) but calls no cudaMalloc, cudaFree
+ * or other allocating routine: its scratch (view constants, work items, work-queue counters) is a
+ * fixed __device__ array of about 4.3 MB inside the library, held by every GPU that loads it
+ * until the process exits. Inputs (textures, created beforehand) and outputs stay the caller's.
+ * Limits: at most STF_NOALLOC_MAX_VIEWS views per call (more -> STF_ERR_INVALID_ARG, nothing
+ * enqueued); work items are coarsened to fit STF_NOALLOC_MAX_ITEMS, which changes no pixel.
+ * The first call on a device looks up the array's device address and uploads a 1 KB table with
+ * a blocking copy: make it before any stream capture. All calls share the array (the counters
+ * are cleared on each call): calls that overlap on the GPU race. Asynchronous on the library
+ * stream otherwise. */
+#define STF_NOALLOC_MAX_VIEWS 256
+#define STF_NOALLOC_MAX_ITEMS 262144
+stf_status stf_render_views_noalloc(const stf_view* views, int n, int filter, int reuse_mode,
+                                    unsigned long long seed);
+
 /* Frees a texture (NULL is a no-op). The caller ensures no enqueued work still reads it. */
 stf_status stf_destroy(stf_texture* tex);
 

@@ -30,6 +30,9 @@ cudaError_t stf_launch_single(const stf::DevView& d, int kind, int mode, cudaStr
 // multi-view scheduler (stf_sched.cu)
 stf_status stf_render_batch(const stf_view* views, int n, int filter, int mode, unsigned long long seed);
 
+// tile shape and schedule of a view, as the multi-view scheduler resolves them (no heap use)
+void stf_resolve_view_config_nohalloc(const stf_view& v, int filter, int mode, int* tw, int* th, int* sched);
+
 // neural decoder (stf_neural.cu)
 stf_status stf_create_neural_texture(const stf_texture_desc* d, stf_texture** out);
 cudaError_t stf_launch_neural_view(const stf::DevView& d, int mode, cudaStream_t s);

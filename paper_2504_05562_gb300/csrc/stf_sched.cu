@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <string_view>
 #include <vector>
 
 #include "stf.h"
@@ -63,7 +64,7 @@ struct TuneEntry {
     int tile_w, tile_h, schedule;
     float ms;
 };
-std::map<std::string, TuneEntry> g_tune;
+std::map<std::string, TuneEntry, std::less<>> g_tune;  // transparent: lookups by string_view
 
 // Area magnification at the view centre: pixels per texel, 1 / sqrt(|det d(texel) / d(pixel)|).
 double view_magnification(const stf_view& v, const stf_texture* t)
@@ -308,6 +309,24 @@ stf_status render_batch_impl(const stf_view* views, int n, int filter, int mode,
 int g_use_graphs = 1;
 
 }  // namespace
+
+// The same resolution as `resolve`, with the class key built in a stack buffer (no heap use).
+void stf_resolve_view_config_nohalloc(const stf_view& v, int filter, int mode, int* tw, int* th, int* sched)
+{
+    const int f = view_filter(v, filter);
+    const double m = view_magnification(v, v.tex);
+    const int mb = m < 2.0 ? 0 : (m < 8.0 ? 1 : (m < 32.0 ? 2 : 3));
+    const long long px = (long long)v.width * v.height;
+    const int rb = px < 500000 ? 0 : (px < 3000000 ? 1 : 2);
+    char buf[96];
+    const int len = snprintf(buf, sizeof buf, "kind%d/filter%d/mode%d/mag%d/res%d", v.tex->kind, f, mode, mb, rb);
+    const auto it = g_tune.find(std::string_view(buf, (size_t)len));
+    *sched = it != g_tune.end() ? it->second.schedule : kDefaultSchedule;
+    if (v.tile_w) { *tw = v.tile_w; *th = v.tile_h; }
+    else if (it != g_tune.end()) { *tw = it->second.tile_w; *th = it->second.tile_h; }
+    else { *tw = 8; *th = 4; }
+    if (mode == STF_MODE_FULL || mode == STF_MODE_ONE_TAP) { *tw = 8; *th = 4; }
+}
 
 stf_status stf_render_batch(const stf_view* views, int n, int filter, int mode, unsigned long long seed)
 {

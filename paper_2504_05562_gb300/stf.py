@@ -52,7 +52,9 @@ EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_str
            "stf_last_error", "stf_version", "stf_decoder_create", "stf_decoder_train", "stf_decoder_gradients",
            "stf_decoder_get_params", "stf_decoder_set_params", "stf_decoder_decode", "stf_decoder_info",
            "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy", "stf_set_option", "stf_get_stat",
-           "stf_autotune", "stf_view_config", "stf_autotune_save", "stf_autotune_load", "stf_autotune_clear")
+           "stf_autotune", "stf_view_config", "stf_autotune_save", "stf_autotune_load", "stf_autotune_clear",
+           "stf_render_views_noalloc")
+NOALLOC_MAX_VIEWS, NOALLOC_MAX_ITEMS = 256, 262144
 OPT_BATCH_GRAPHS = 1
 STAT_GRAPH_BUILDS, STAT_GRAPH_REPLAYS = 1, 2
 
@@ -93,8 +95,9 @@ def _bind_extra(L):
     L.stf_autotune_save.argtypes = [C.c_char_p]
     L.stf_autotune_load.argtypes = [C.c_char_p]
     L.stf_autotune_clear.argtypes = []
+    L.stf_render_views_noalloc.argtypes = [C.POINTER(View), C.c_int, C.c_int, C.c_int, C.c_ulonglong]
     for n in ("stf_set_option", "stf_get_stat", "stf_autotune", "stf_view_config", "stf_autotune_save",
-              "stf_autotune_load", "stf_autotune_clear"):
+              "stf_autotune_load", "stf_autotune_clear", "stf_render_views_noalloc"):
         getattr(L, n).restype = C.c_int
 
 
@@ -219,6 +222,13 @@ def render_views(views, filter=FILTER_PER_VIEW, mode=MODE_WAVE3, seed=0):
     """views: a sequence of View structs (make_view). Enqueues the work on the library stream."""
     arr = (View * len(views))(*views)
     _check(load().stf_render_views(arr, len(views), int(filter), int(mode), int(seed) & (2 ** 64 - 1)))
+
+
+def render_views_noalloc(views, filter=FILTER_PER_VIEW, mode=MODE_WAVE3, seed=0):
+    """Same as render_views, through the allocation-free entry point (fixed scratch inside the
+    library, at most NOALLOC_MAX_VIEWS views)."""
+    arr = (View * len(views))(*views)
+    _check(load().stf_render_views_noalloc(arr, len(views), int(filter), int(mode), int(seed) & (2 ** 64 - 1)))
 
 
 def render(tex: Texture, view: dict, mode, seed=0, debug=False, out=None, filter=FILTER_PER_VIEW):
