@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--tex", type=int, default=2048)
     p.add_argument("--no-extras", action="store_true", help="skip comparators, PSNR, e2e and CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-neural", action="store_true", help="skip the neural-decoder (config 4) extra")
+    p.add_argument("--no-batch", action="store_true", help="skip the 64-view batch (config 5) extra")
+    p.add_argument("--neural-steps", type=int, default=2000)
     return p.parse_args()
 
 
@@ -163,16 +166,18 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def time_mode(stf, torch, tex, view_base, mode, steps, warmup, flush, rank, out):
-    """Per-launch CUDA-event times (ms) of `steps` frames after `warmup` frames; L2 flushed first."""
+def time_mode(stf, torch, tex, view_base, mode, steps, warmup, flush, rank, out, world=1):
+    """Per-launch CUDA-event times (ms) of `steps` frames after `warmup` frames; L2 flushed first.
+    Each rank renders its own frames (replicas)."""
+    from paper_2504_05562_gb300 import replicas
     stream = torch.cuda.current_stream()
     for i in range(warmup):
-        v = dict(view_base, frame=i % 65536)
+        v = dict(view_base, frame=(60000 + i) % 65536)
         stf.render_views([stf.make_view(v, tex, out)], stf.FILTER_PER_VIEW, mode, 0)
     torch.cuda.synchronize()
     times = []
-    for i in range(steps):
-        v = dict(view_base, frame=(rank * steps + i) % 65536)
+    for f in replicas.frames_for_rank(rank, world, steps):
+        v = dict(view_base, frame=f)
         cv = stf.make_view(v, tex, out)
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -274,26 +279,21 @@ def run_ours(a):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     mode = MODES[a.mode]
 
+    from paper_2504_05562_gb300 import replicas
+
     def barrier():
         torch.cuda.synchronize()
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        replicas.barrier()
 
     # headline: the reuse mode
-    time_mode(stf, torch, tex, view, mode, 0, a.warmup, flush, rank, out)
+    time_mode(stf, torch, tex, view, mode, 0, a.warmup, flush, rank, out, world)
     barrier()
     with Clocks(local_rank) as clk:
         t_wall = time.perf_counter()
-        times = time_mode(stf, torch, tex, view, mode, a.steps, 0, flush, rank, out)
+        times = time_mode(stf, torch, tex, view, mode, a.steps, 0, flush, rank, out, world)
         barrier()
         t_wall = time.perf_counter() - t_wall
-    dev_ms = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = t.item()
+    dev_ms = replicas.max_over_ranks(sum(times), device="cuda")
     ms = dev_ms / a.steps
     px_all = a.width * a.height * a.steps * world
     value = px_all / (dev_ms * 1e-3) / 1e9
@@ -339,6 +339,10 @@ def run_ours(a):
         line["modes"] = extras
         line["reuse_time_over_one_tap"] = extras[a.mode]["ms_median"] / extras["one_tap"]["ms_median"]
         line["e2e"] = e2e(a, stf, torch, mat, view)
+        if not a.no_neural:
+            line["neural"] = neural_extra(a, stf, torch, W, view, flush)
+        if not a.no_batch:
+            line["batch"] = batch_extra(a, stf, torch, W, tex if a.fmt == "fp16" and a.tex == 2048 else None, flush)
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(a, mat, view, a.cpu_seconds)
     if rank == 0:
@@ -347,6 +351,122 @@ def run_ours(a):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def time_fn(torch, fn, steps, warmup, flush):
+    """CUDA-event time (ms) of fn() per call, L2 flushed before each timed call."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return [x.elapsed_time(y) for x, y in ev]
+
+
+def neural_extra(a, stf, torch, W, view, flush):
+    """Config 4: a 2048^2 8-channel material compressed into a 512^2 x 16 FP16 latent grid and an
+    MLP 24-64-64-8 trained on the GPU; the 4K frame rendered with one tensor-core decode per
+    pixel (one-tap and reuse) or four (full bilinear). PSNR of the decoded texels against the FP32
+    material, and of each rendered frame against the full filter of the uncompressed material."""
+    import numpy as np
+    from paper_2504_05562_gb300 import neural
+    src = W.brick_material(a.tex).astype(np.float32)
+    target = stf.Texture(W.make_material(src, W.FP32))
+    dec = neural.Decoder(a.tex, a.tex, a.tex // 4, a.tex // 4, batch=65536, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = dec.train(target, a.neural_steps)
+    train_s = time.perf_counter() - t0
+    # decoded-texel PSNR over all texels (chunks of 1M)
+    n = a.tex * a.tex
+    se = 0.0
+    srct = torch.from_numpy(src.reshape(-1, 8)).cuda()
+    for c0 in range(0, n, 1 << 20):
+        idx = torch.arange(c0, min(n, c0 + (1 << 20)), dtype=torch.int64, device="cuda")
+        packed = ((idx % a.tex) | ((idx // a.tex) << 16)).to(torch.int32)
+        d = dec.decode(packed)
+        se += float(((d.double() - srct[c0:c0 + d.shape[0]].double()) ** 2).sum())
+    decode_psnr = 10 * np.log10(1.0 / (se / (n * 8)))
+    ntex = dec.texture()
+    out = torch.empty((a.height, a.width, 4), dtype=torch.float32, device="cuda")
+    res = {}
+    imgs = {}
+    for name in ("one_tap", a.mode, "full"):
+        m = MODES[name]
+        cv = stf.make_view(dict(view, frame=0), ntex, out)
+        tt = time_fn(torch, lambda: stf.render_views([cv], stf.FILTER_PER_VIEW, m, 0), max(5, a.steps // 2), 3, flush)
+        img = torch.empty_like(out)
+        stf.render_views([stf.make_view(dict(view, frame=0), ntex, img)], stf.FILTER_PER_VIEW, m, 0)
+        imgs[name] = img
+        res[name] = {"ms_median": statistics.median(tt), "gpix_s": a.width * a.height / (statistics.median(tt) * 1e-3) / 1e9}
+    # the uncompressed material's full filter is the judge of the neural frames
+    ref = torch.empty_like(out)
+    stf.render_views([stf.make_view(dict(view, frame=0), target, ref)], stf.FILTER_PER_VIEW, MODES["full"], 0)
+    torch.cuda.synchronize()
+    for name in res:
+        res[name]["psnr_db_vs_uncompressed_full"] = psnr(torch, imgs[name], ref)
+        if name != "full":
+            res[name]["psnr_db_vs_neural_full"] = psnr(torch, imgs[name], imgs["full"])
+    flops_px = 2 * (32 * 64 + 64 * 64 + 64 * 8)  # executed MACs x 2 (24 inputs padded to 32)
+    ms1 = res["one_tap"]["ms_median"]
+    return {"workload": "c4-4k: %dx%d, %d^2 material, %d^2x16 FP16 latents + MLP 24-64-64-8, %s"
+                        % (a.width, a.height, a.tex, a.tex // 4, a.filter),
+            "train_steps": a.neural_steps, "train_batch": 65536, "train_s": train_s,
+            "loss_first": float(losses[0]) if len(losses) else None,
+            "loss_last": float(losses[-1]) if len(losses) else None,
+            "decode_psnr_db": decode_psnr, "modes": res,
+            "reuse_time_over_one_tap": res[a.mode]["ms_median"] / ms1,
+            "full_time_over_one_tap": res["full"]["ms_median"] / ms1,
+            "decode_tflops_one_tap": a.width * a.height * flops_px / (ms1 * 1e-3) / 1e12,
+            "tensor_peak_tflops_bf16_measured": load_peaks().get("bf16_tflops")}
+
+
+def batch_extra(a, stf, torch, W, tex, flush):
+    """Config 5: 64 views of mixed resolution, magnification and filter over the shared FP16
+    material in one persistent launch (CUDA-graph replay), after autotuning the tile shape and
+    schedule per view class. Reported as total Gpix/s and mean time per view, beside the same
+    views rendered one launch each."""
+    if tex is None:
+        tex = stf.Texture(W.material_c3(W.FP16))
+    views = W.config5_views(64)
+    for v in views:
+        v["tile"] = (0, 0)
+    outs = [torch.empty((v["height"], v["width"], 4), dtype=torch.float32, device="cuda") for v in views]
+    cvs = [stf.make_view(v, tex, o) for v, o in zip(views, outs)]
+    px = sum(v["width"] * v["height"] for v in views)
+    mode = MODES[a.mode]
+    stf.autotune_clear()
+    t0 = time.perf_counter()
+    stf.autotune(cvs, stf.FILTER_PER_VIEW, mode, 0)
+    tune_s = time.perf_counter() - t0
+    configs = {}
+    for c in cvs:
+        k = "%dx%d/s%d" % stf.view_config(c, stf.FILTER_PER_VIEW, mode)
+        configs[k] = configs.get(k, 0) + 1
+    b0 = stf.get_stat(stf.STAT_GRAPH_BUILDS)
+    tb = time_fn(torch, lambda: stf.render_views(cvs, stf.FILTER_PER_VIEW, mode, 0), 5, 3, flush)
+    builds = stf.get_stat(stf.STAT_GRAPH_BUILDS) - b0
+
+    def each():
+        for c in cvs:
+            stf.render_views([c], stf.FILTER_PER_VIEW, mode, 0)
+    te = time_fn(torch, each, 3, 1, flush)
+    stf.autotune_clear()
+    mb, me = statistics.median(tb), statistics.median(te)
+    return {"workload": "c5: 64 views, resolutions from {256^2, 1280x720, 1920x1080, 3840x2160}, "
+                        "magnification log-uniform 1-64x, bilinear/B-spline per view, FP16 2048^2 material, %s" % a.mode,
+            "pixels": px, "ms_median": mb, "gpix_s": px / (mb * 1e-3) / 1e9, "ms_per_view_mean": mb / 64,
+            "one_launch_per_view_ms": me, "one_launch_per_view_gpix_s": px / (me * 1e-3) / 1e9,
+            "autotune_s": tune_s, "tuned_configs": configs, "graph_builds_during_timing": builds,
+            "gpu_launches_per_batch": 1}
 
 
 def e2e(a, stf, torch, mat, view):
