@@ -188,7 +188,7 @@ stf_status stf_autotune_clear(void);
  * cudaMalloc / cudaFree can synchronise the device and can fail mid-frame. Renders the batch
  * exactly as stf_render_views does (same kernels, same pixels) but calls no cudaMalloc, cudaFree
  * or other allocating routine: its scratch (view constants, work items, work-queue counters) is a
- * fixed __device__ array of about 4.3 MB inside the library, held by every GPU that loads it
+ * fixed __device__ array of about 4.2 MB inside the library, held by every GPU that loads it
  * until the process exits. Inputs (textures, created beforehand) and outputs stay the caller's.
  * Limits: at most STF_NOALLOC_MAX_VIEWS views per call (more -> STF_ERR_INVALID_ARG, nothing
  * enqueued); work items are coarsened to fit STF_NOALLOC_MAX_ITEMS, which changes no pixel.
@@ -196,7 +196,7 @@ stf_status stf_autotune_clear(void);
  * a blocking copy: make it before any stream capture. All calls share the array (the counters
  * are cleared on each call): calls that overlap on the GPU race. Asynchronous on the library
  * stream otherwise. */
-#define STF_NOALLOC_MAX_VIEWS 256
+#define STF_NOALLOC_MAX_VIEWS 224
 #define STF_NOALLOC_MAX_ITEMS 262144
 stf_status stf_render_views_noalloc(const stf_view* views, int n, int filter, int reuse_mode,
                                     unsigned long long seed);

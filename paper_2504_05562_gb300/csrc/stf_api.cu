@@ -415,6 +415,12 @@ extern "C" stf_status stf_render_views(const stf_view* views, int n, int filter,
     if (n > 1) return stf_render_batch(views, n, filter, reuse_mode, seed);
     DevView d;
     stf_fill_devview(views[0], filter, reuse_mode, seed, lut, d);
+    int tw, th, sched;  // a 0x0 tile takes the autotuned shape of the view's class
+    stf_resolve_view_config_nohalloc(views[0], filter, reuse_mode, &tw, &th, &sched);
+    d.tile_w = tw;
+    d.tile_h = th;
+    d.tiles_x = (d.width + tw - 1) / tw;
+    d.tiles_y = (d.height + th - 1) / th;
     cudaError_t e = stf_launch_single(d, views[0].tex->kind, reuse_mode, g_stream);
     if (e != cudaSuccess) return stf_cuda_fail(e, "render launch");
     return STF_OK;

@@ -169,9 +169,10 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
 // decoded channels); the 48-byte stride keeps 128-bit reads of neighbouring lanes conflict-free.
 constexpr int kRecPerLane = 3;
 
-// Blocks resident per SM the kernel is compiled for: the neural decode is register-heavy and
-// needs at least two 8-warp blocks per SM to hide the tensor-core latency.
-template <int KIND> struct MinBlocks { static constexpr int n = 1; };
+// Blocks resident per SM the kernel is compiled for (caps registers per thread at 65536 /
+// (256 n)): five 8-warp blocks (<= 51 registers) keep the issue-bound texture kinds at 40 warps
+// per SM; the register-heavy neural decode gets two (<= 128 registers).
+template <int KIND> struct MinBlocks { static constexpr int n = 5; };
 template <> struct MinBlocks<K_NEURAL> { static constexpr int n = 2; };
 
 // One view: block (bx, by) holds 8 warps on tile row by, tiles bx * 8 .. bx * 8 + 7.

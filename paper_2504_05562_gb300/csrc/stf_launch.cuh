@@ -49,37 +49,22 @@ cudaError_t launch_view_kind(const DevView& v, int mode, cudaStream_t s)
 
 // ------------------------------------------------------------------------------ multi-view
 
-// One tile of any view of a batch: the view's filter and tile shape select the instance.
-template <int KIND, int MODE>
-__device__ __forceinline__ void render_tile_any(const DevView& v, int variant, int tx, int ty, int lane, float4* rec,
-                                                float* wtab, unsigned char* scratch)
-{
-    if constexpr (MODE <= 1) {
-        if (variant < 3) render_tile<KIND, 0, MODE, 8, 4>(v, tx, ty, lane, rec, wtab, scratch);
-        else render_tile<KIND, 1, MODE, 8, 4>(v, tx, ty, lane, rec, wtab, scratch);
-    } else {
-        switch (variant) {
-        case 0: render_tile<KIND, 0, MODE, 8, 4>(v, tx, ty, lane, rec, wtab, scratch); break;
-        case 1: render_tile<KIND, 0, MODE, 4, 8>(v, tx, ty, lane, rec, wtab, scratch); break;
-        case 2: render_tile<KIND, 0, MODE, 16, 2>(v, tx, ty, lane, rec, wtab, scratch); break;
-        case 3: render_tile<KIND, 1, MODE, 8, 4>(v, tx, ty, lane, rec, wtab, scratch); break;
-        case 4: render_tile<KIND, 1, MODE, 4, 8>(v, tx, ty, lane, rec, wtab, scratch); break;
-        default: render_tile<KIND, 1, MODE, 16, 2>(v, tx, ty, lane, rec, wtab, scratch); break;
-        }
-    }
-}
+// The view constants of a batch, one copy per material-kind module (each stf_kind_*.cu includes
+// this header once): reads with a block-uniform view index are served by the constant cache like
+// kernel parameters, at no issue cost.
+static __constant__ DevView c_batch_views[kBatchMaxViews];
 
-// Persistent multi-view kernel: each block pulls work items (a run of tiles of one view) from a
-// device counter until the list is exhausted; the view's constants are staged in shared memory.
-// Nothing waits on another block, so no wait can stall.
-template <int KIND, int MODE>
+// Persistent multi-view kernel for one (filter, tile shape) variant: each block pulls work items
+// (a run of tiles of one view) from a device counter until the list is exhausted. Nothing waits
+// on another block, so no wait can stall. One kernel per variant keeps the code of a launch as
+// small as a single-view kernel's.
+template <int KIND, int MODE, int F, int TW, int TH>
 __global__ void __launch_bounds__(256, MinBlocks<KIND>::n)
-    k_render_batch(const DevView* __restrict__ views, const WorkItem* __restrict__ items, int n_items, int* counter)
+    k_render_batch(const WorkItem* __restrict__ items, int n_items, int* counter)
 {
     __shared__ float4 recs[kWarpsPerBlock * 32 * kRecPerLane];
     __shared__ float wtabs[kWarpsPerBlock * 32 * 8];
     __shared__ __align__(16) unsigned char scratch[kWarpsPerBlock * DecodeScratch<KIND>::bytes];
-    __shared__ DevView sv;
     __shared__ WorkItem sw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
@@ -89,45 +74,70 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND>::n)
         }
         __syncthreads();
         const WorkItem w = sw;
+        __syncthreads();  // sw is rewritten by the next pull
         if (w.view < 0) break;
-        {
-            const int* src = reinterpret_cast<const int*>(views + w.view);
-            int* dst = reinterpret_cast<int*>(&sv);
-            for (int i = threadIdx.x; i < (int)(sizeof(DevView) / 4); i += blockDim.x) dst[i] = src[i];
-        }
-        __syncthreads();
+        const DevView& v = c_batch_views[w.view];
         for (int t = w.tile0 + warp; t < w.tile0 + w.ntiles; t += kWarpsPerBlock) {
-            const int ty = t / sv.tiles_x;
-            render_tile_any<KIND, MODE>(sv, w.variant, t - ty * sv.tiles_x, ty, lane, recs + warp * 32 * kRecPerLane,
-                                        wtabs + warp * 32 * 8, scratch + warp * DecodeScratch<KIND>::bytes);
+            const int ty = t / v.tiles_x;
+            render_tile<KIND, F, MODE, TW, TH>(v, t - ty * v.tiles_x, ty, lane, recs + warp * 32 * kRecPerLane,
+                                               wtabs + warp * 32 * 8, scratch + warp * DecodeScratch<KIND>::bytes);
         }
-        __syncthreads();  // sv and sw are rewritten for the next item
     }
 }
 
 // grid > 0 launches; grid == 0 only reports the instance's resident blocks per SM in *per_sm.
-template <int KIND, int MODE>
-static cudaError_t launch_batch_mode(const DevView* views, const WorkItem* items, int n_items, int* counter, int grid,
-                                     int* per_sm, cudaStream_t s)
+template <int KIND, int MODE, int F, int TW, int TH>
+static cudaError_t launch_batch_v(const WorkItem* items, int n_items, int* counter, int grid, int* per_sm, cudaStream_t s)
 {
-    if (grid == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE>, 256, 0);
-    k_render_batch<KIND, MODE><<<grid, 256, 0, s>>>(views, items, n_items, counter);
+    if (grid == 0)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE, F, TW, TH>, 256, 0);
+    k_render_batch<KIND, MODE, F, TW, TH><<<grid, 256, 0, s>>>(items, n_items, counter);
     return cudaGetLastError();
 }
 
+// variant = filter * 3 + tile shape (0: 8x4, 1: 4x8, 2: 16x2); without sharing only 8x4 exists.
+template <int KIND, int MODE>
+static cudaError_t launch_batch_mode(const WorkItem* items, int n_items, int* counter, int grid, int variant, int* per_sm,
+                                     cudaStream_t s)
+{
+    if constexpr (MODE <= 1) {
+        if (variant == 0) return launch_batch_v<KIND, MODE, 0, 8, 4>(items, n_items, counter, grid, per_sm, s);
+        if (variant == 3) return launch_batch_v<KIND, MODE, 1, 8, 4>(items, n_items, counter, grid, per_sm, s);
+        return cudaErrorInvalidValue;
+    } else {
+        switch (variant) {
+        case 0: return launch_batch_v<KIND, MODE, 0, 8, 4>(items, n_items, counter, grid, per_sm, s);
+        case 1: return launch_batch_v<KIND, MODE, 0, 4, 8>(items, n_items, counter, grid, per_sm, s);
+        case 2: return launch_batch_v<KIND, MODE, 0, 16, 2>(items, n_items, counter, grid, per_sm, s);
+        case 3: return launch_batch_v<KIND, MODE, 1, 8, 4>(items, n_items, counter, grid, per_sm, s);
+        case 4: return launch_batch_v<KIND, MODE, 1, 4, 8>(items, n_items, counter, grid, per_sm, s);
+        case 5: return launch_batch_v<KIND, MODE, 1, 16, 2>(items, n_items, counter, grid, per_sm, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <int KIND>
-cudaError_t launch_batch_kind(const DevView* views, const WorkItem* items, int n_items, int* counter, int grid, int mode,
+cudaError_t launch_batch_kind(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant,
                               int* per_sm, cudaStream_t s)
 {
     switch (mode) {
-    case 0: return launch_batch_mode<KIND, 0>(views, items, n_items, counter, grid, per_sm, s);
-    case 1: return launch_batch_mode<KIND, 1>(views, items, n_items, counter, grid, per_sm, s);
-    case 2: return launch_batch_mode<KIND, 2>(views, items, n_items, counter, grid, per_sm, s);
-    case 3: return launch_batch_mode<KIND, 3>(views, items, n_items, counter, grid, per_sm, s);
-    case 4: return launch_batch_mode<KIND, 4>(views, items, n_items, counter, grid, per_sm, s);
-    case 5: return launch_batch_mode<KIND, 5>(views, items, n_items, counter, grid, per_sm, s);
+    case 0: return launch_batch_mode<KIND, 0>(items, n_items, counter, grid, variant, per_sm, s);
+    case 1: return launch_batch_mode<KIND, 1>(items, n_items, counter, grid, variant, per_sm, s);
+    case 2: return launch_batch_mode<KIND, 2>(items, n_items, counter, grid, variant, per_sm, s);
+    case 3: return launch_batch_mode<KIND, 3>(items, n_items, counter, grid, variant, per_sm, s);
+    case 4: return launch_batch_mode<KIND, 4>(items, n_items, counter, grid, variant, per_sm, s);
+    case 5: return launch_batch_mode<KIND, 5>(items, n_items, counter, grid, variant, per_sm, s);
     }
     return cudaErrorInvalidValue;
+}
+
+// Copies a batch's view constants (device memory, at most kBatchMaxViews) into this module's
+// constant bank on stream s.
+static cudaError_t set_batch_views(const DevView* views, int n_views, cudaStream_t s)
+{
+    if (n_views < 1 || n_views > kBatchMaxViews) return cudaErrorInvalidValue;
+    return cudaMemcpyToSymbolAsync(c_batch_views, views, (size_t)n_views * sizeof(DevView), 0, cudaMemcpyDeviceToDevice, s);
 }
 
 }  // namespace stf
@@ -135,9 +145,13 @@ cudaError_t launch_batch_kind(const DevView* views, const WorkItem* items, int n
 #define STF_INSTANTIATE_KIND(KIND, NAME)                                                        \
     namespace stf {                                                                             \
     cudaError_t NAME(const DevView& v, int mode, cudaStream_t s) { return launch_view_kind<KIND>(v, mode, s); } \
-    cudaError_t NAME##_batch(const DevView* views, const WorkItem* items, int n_items, int* counter, int grid, \
-                             int mode, int* per_sm, cudaStream_t s)                             \
+    cudaError_t NAME##_batch(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant, \
+                             int* per_sm, cudaStream_t s)                                       \
     {                                                                                           \
-        return launch_batch_kind<KIND>(views, items, n_items, counter, grid, mode, per_sm, s); \
+        return launch_batch_kind<KIND>(items, n_items, counter, grid, mode, variant, per_sm, s); \
+    }                                                                                           \
+    cudaError_t NAME##_batch_views(const DevView* views, int n_views, cudaStream_t s)           \
+    {                                                                                           \
+        return set_batch_views(views, n_views, s);                                              \
     }                                                                                           \
     }

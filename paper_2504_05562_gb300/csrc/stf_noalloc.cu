@@ -26,9 +26,10 @@
 using namespace stf;
 
 namespace stf {
-#define STF_DECLARE_BATCH_NA(NAME)                                                                          \
-    cudaError_t NAME##_batch(const DevView* views, const WorkItem* items, int n_items, int* counter, int grid, \
-                             int mode, int* per_sm, cudaStream_t s);
+#define STF_DECLARE_BATCH_NA(NAME)                                                                           \
+    cudaError_t NAME##_batch(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant, \
+                             int* per_sm, cudaStream_t s);                                                     \
+    cudaError_t NAME##_batch_views(const DevView* views, int n_views, cudaStream_t s);
 STF_DECLARE_BATCH_NA(launch_view_F32x4)
 STF_DECLARE_BATCH_NA(launch_view_F32x8)
 STF_DECLARE_BATCH_NA(launch_view_F16x4)
@@ -41,12 +42,15 @@ STF_DECLARE_BATCH_NA(launch_view_NEURAL)
 
 namespace {
 
+constexpr int kVariants = 6;
+
 struct NoallocScratch {
     DevView views[STF_NOALLOC_MAX_VIEWS];
     WorkItem items[STF_NOALLOC_MAX_ITEMS];
     float unorm_lut[256];
-    int counters[K_COUNT];
+    int counters[K_COUNT * kVariants];
 };
+static_assert(STF_NOALLOC_MAX_VIEWS <= kBatchMaxViews, "one persistent launch per material kind");
 
 // The scratch, one copy per device that loads the library.
 __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
@@ -56,20 +60,28 @@ NoallocScratch* g_dev_ptr[kMaxDevices];  // device address of g_noalloc_scratch,
 NoallocScratch g_stage;                  // host-side lists (static: no heap use)
 int g_order[STF_NOALLOC_MAX_VIEWS];
 
-cudaError_t launch_batch_na(int kind, const DevView* views, const WorkItem* items, int n_items, int* counter, int grid,
-                            int mode, int* per_sm, cudaStream_t s)
-{
-    switch (kind) {
-    case K_F32x4: return launch_view_F32x4_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_F32x8: return launch_view_F32x8_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_F16x4: return launch_view_F16x4_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_F16x8: return launch_view_F16x8_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_BF16x8: return launch_view_BF16x8_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_E4M3x8: return launch_view_E4M3x8_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_U8x4_F16x2: return launch_view_U8x4_F16x2_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_NEURAL: return launch_view_NEURAL_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    }
+#define STF_KIND_SWITCH_NA(CALL)                                   \
+    switch (kind) {                                                \
+    case K_F32x4: return launch_view_F32x4_##CALL;                 \
+    case K_F32x8: return launch_view_F32x8_##CALL;                 \
+    case K_F16x4: return launch_view_F16x4_##CALL;                 \
+    case K_F16x8: return launch_view_F16x8_##CALL;                 \
+    case K_BF16x8: return launch_view_BF16x8_##CALL;               \
+    case K_E4M3x8: return launch_view_E4M3x8_##CALL;               \
+    case K_U8x4_F16x2: return launch_view_U8x4_F16x2_##CALL;       \
+    case K_NEURAL: return launch_view_NEURAL_##CALL;               \
+    }                                                              \
     return cudaErrorInvalidValue;
+
+cudaError_t launch_batch_na(int kind, const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant,
+                            int* per_sm, cudaStream_t s)
+{
+    STF_KIND_SWITCH_NA(batch(items, n_items, counter, grid, mode, variant, per_sm, s))
+}
+
+cudaError_t set_views_na(int kind, const DevView* views, int n_views, cudaStream_t s)
+{
+    STF_KIND_SWITCH_NA(batch_views(views, n_views, s))
 }
 
 // Once per device, with that device current: the scratch's device address and its UNORM8 table.
@@ -123,7 +135,7 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
     const float* lut = dev->unorm_lut;
 
     // views grouped by material kind, each group costliest first (the order stf_render_views uses)
-    int group_start[K_COUNT + 1], group_items[K_COUNT], total_tiles[STF_NOALLOC_MAX_VIEWS];
+    int group_start[K_COUNT + 1], total_tiles[STF_NOALLOC_MAX_VIEWS];
     int tw[STF_NOALLOC_MAX_VIEWS], th[STF_NOALLOC_MAX_VIEWS], sc[STF_NOALLOC_MAX_VIEWS];
     double cost[STF_NOALLOC_MAX_VIEWS];
     for (int i = 0; i < n; ++i) {
@@ -145,6 +157,8 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
         coarsen *= 2;
     }
     int nv = 0, ni = 0;
+    int var_of[STF_NOALLOC_MAX_VIEWS];
+    int sub_start[K_COUNT][kVariants + 1];
     group_start[0] = 0;
     for (int k = 0; k < K_COUNT; ++k) {
         const int v0 = nv;
@@ -156,7 +170,6 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
             while (b >= v0 && cost[g_order[b]] < cost[x]) { g_order[b + 1] = g_order[b]; --b; }
             g_order[b + 1] = x;
         }
-        const int i0 = ni;
         for (int j = v0; j < nv; ++j) {
             const int i = g_order[j];
             DevView& d = g_stage.views[j];
@@ -165,13 +178,20 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
             d.tile_h = th[i];
             d.tiles_x = (d.width + tw[i] - 1) / tw[i];
             d.tiles_y = (d.height + th[i] - 1) / th[i];
-            const int variant = (filter == STF_FILTER_PER_VIEW ? views[i].filter : filter) * 3 +
-                                (tw[i] == 8 ? 0 : (tw[i] == 4 ? 1 : 2));
-            const int per = (int)((long long)kWarpsPerBlock * sc[i] * coarsen);
-            for (int t0 = 0; t0 < total_tiles[i]; t0 += per)
-                g_stage.items[ni++] = WorkItem{j - v0, t0, total_tiles[i] - t0 < per ? total_tiles[i] - t0 : per, variant};
+            var_of[j] = (filter == STF_FILTER_PER_VIEW ? views[i].filter : filter) * 3 + (tw[i] == 8 ? 0 : (tw[i] == 4 ? 1 : 2));
         }
-        group_items[k] = ni - i0;
+        // items of the group, contiguous per variant (one persistent kernel per variant)
+        for (int var = 0; var < kVariants; ++var) {
+            sub_start[k][var] = ni;
+            for (int j = v0; j < nv; ++j) {
+                if (var_of[j] != var) continue;
+                const int i = g_order[j];
+                const int per = (int)((long long)kWarpsPerBlock * sc[i] * coarsen);
+                for (int t0 = 0; t0 < total_tiles[i]; t0 += per)
+                    g_stage.items[ni++] = WorkItem{j - v0, t0, total_tiles[i] - t0 < per ? total_tiles[i] - t0 : per, var};
+            }
+        }
+        sub_start[k][kVariants] = ni;
         group_start[k + 1] = nv;
     }
 
@@ -180,19 +200,23 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
     if (e == cudaSuccess) e = cudaMemcpyAsync(dev->items, g_stage.items, (size_t)ni * sizeof(WorkItem), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dev->counters, 0, sizeof dev->counters, s);
     if (e != cudaSuccess) return stf_cuda_fail(e, "no-alloc batch upload");
-    int item_base = 0;
     for (int k = 0; k < K_COUNT; ++k) {
         const int nvk = group_start[k + 1] - group_start[k];
         if (nvk == 0) continue;
-        int per_sm = 0;
-        e = launch_batch_na(k, nullptr, nullptr, 0, nullptr, 0, reuse_mode, &per_sm, s);
-        if (e != cudaSuccess) return stf_cuda_fail(e, "occupancy query");
-        int grid = (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm)) * sm_count_na();
-        if (grid > group_items[k]) grid = group_items[k];
-        e = launch_batch_na(k, dev->views + group_start[k], dev->items + item_base, group_items[k], dev->counters + k, grid,
-                            reuse_mode, &per_sm, s);
-        if (e != cudaSuccess) return stf_cuda_fail(e, "no-alloc batch launch");
-        item_base += group_items[k];
+        e = set_views_na(k, dev->views + group_start[k], nvk, s);
+        if (e != cudaSuccess) return stf_cuda_fail(e, "no-alloc view upload");
+        for (int var = 0; var < kVariants; ++var) {
+            const int nitems = sub_start[k][var + 1] - sub_start[k][var];
+            if (nitems == 0) continue;
+            int per_sm = 0;
+            e = launch_batch_na(k, nullptr, 0, nullptr, 0, reuse_mode, var, &per_sm, s);
+            if (e != cudaSuccess) return stf_cuda_fail(e, "occupancy query");
+            int grid = (per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm)) * sm_count_na();
+            if (grid > nitems) grid = nitems;
+            e = launch_batch_na(k, dev->items + sub_start[k][var], nitems, dev->counters + k * kVariants + var, grid,
+                                reuse_mode, var, &per_sm, s);
+            if (e != cudaSuccess) return stf_cuda_fail(e, "no-alloc batch launch");
+        }
     }
     return STF_OK;
 }

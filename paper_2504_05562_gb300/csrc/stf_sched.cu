@@ -23,9 +23,10 @@
 using namespace stf;
 
 namespace stf {
-#define STF_DECLARE_BATCH(NAME)                                                                             \
-    cudaError_t NAME##_batch(const DevView* views, const WorkItem* items, int n_items, int* counter, int grid, \
-                             int mode, int* per_sm, cudaStream_t s);
+#define STF_DECLARE_BATCH(NAME)                                                                              \
+    cudaError_t NAME##_batch(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant, \
+                             int* per_sm, cudaStream_t s);                                                     \
+    cudaError_t NAME##_batch_views(const DevView* views, int n_views, cudaStream_t s);
 STF_DECLARE_BATCH(launch_view_F32x4)
 STF_DECLARE_BATCH(launch_view_F32x8)
 STF_DECLARE_BATCH(launch_view_F16x4)
@@ -38,20 +39,28 @@ STF_DECLARE_BATCH(launch_view_NEURAL)
 
 namespace {
 
-cudaError_t launch_batch(int kind, const DevView* views, const WorkItem* items, int n_items, int* counter, int grid,
-                         int mode, int* per_sm, cudaStream_t s)
-{
-    switch (kind) {
-    case K_F32x4: return launch_view_F32x4_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_F32x8: return launch_view_F32x8_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_F16x4: return launch_view_F16x4_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_F16x8: return launch_view_F16x8_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_BF16x8: return launch_view_BF16x8_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_E4M3x8: return launch_view_E4M3x8_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_U8x4_F16x2: return launch_view_U8x4_F16x2_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    case K_NEURAL: return launch_view_NEURAL_batch(views, items, n_items, counter, grid, mode, per_sm, s);
-    }
+#define STF_KIND_SWITCH(CALL)                                      \
+    switch (kind) {                                                \
+    case K_F32x4: return launch_view_F32x4_##CALL;                 \
+    case K_F32x8: return launch_view_F32x8_##CALL;                 \
+    case K_F16x4: return launch_view_F16x4_##CALL;                 \
+    case K_F16x8: return launch_view_F16x8_##CALL;                 \
+    case K_BF16x8: return launch_view_BF16x8_##CALL;               \
+    case K_E4M3x8: return launch_view_E4M3x8_##CALL;               \
+    case K_U8x4_F16x2: return launch_view_U8x4_F16x2_##CALL;       \
+    case K_NEURAL: return launch_view_NEURAL_##CALL;               \
+    }                                                              \
     return cudaErrorInvalidValue;
+
+cudaError_t launch_batch(int kind, const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant,
+                         int* per_sm, cudaStream_t s)
+{
+    STF_KIND_SWITCH(batch(items, n_items, counter, grid, mode, variant, per_sm, s))
+}
+
+cudaError_t set_views(int kind, const DevView* views, int n_views, cudaStream_t s)
+{
+    STF_KIND_SWITCH(batch_views(views, n_views, s))
 }
 
 // ------------------------------------------------------------------------------ view classes
@@ -114,22 +123,32 @@ int tile_code(int tw, int th) { return tw == 8 ? 0 : (tw == 4 ? 1 : 2); }
 
 // ------------------------------------------------------------------------------ batches
 
-struct Group {
-    int kind;
-    std::vector<int> views;   // indices into the caller's array, costliest first
+struct Sub {  // the items of one (filter, tile shape) variant within a group
+    int variant;
     std::vector<WorkItem> items;
-    size_t views_off, items_off;  // byte offsets in the staging / device buffer
-    int grid;
+    size_t items_off;
+    int grid, counter;
 };
+
+struct Group {  // views of one material kind, at most kBatchMaxViews, costliest first
+    int kind;
+    std::vector<int> views;
+    std::vector<Sub> subs;
+    size_t views_off;
+};
+
+constexpr int kBranches = 6;  // concurrent variant kernels of a group
 
 struct BatchState {
     int device = -1;
     cudaStream_t cap = nullptr;
+    cudaStream_t branch[kBranches] = {};
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
     unsigned char* host[2] = {nullptr, nullptr};  // pinned staging
     unsigned char* dev[2] = {nullptr, nullptr};
     int* counters[2] = {nullptr, nullptr};
     size_t cap_bytes = 0;
-    int cap_groups = 0;
+    int cap_counters = 0;
     cudaEvent_t done[2] = {nullptr, nullptr};
     bool used[2] = {false, false};
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -151,7 +170,7 @@ int sm_count()
     return n;
 }
 
-stf_status ensure_buffers(size_t bytes, int groups)
+stf_status ensure_buffers(size_t bytes, int counters)
 {
     BatchState& b = g_batch;
     int dev = 0;
@@ -161,10 +180,18 @@ stf_status ensure_buffers(size_t bytes, int groups)
     cudaError_t e;
     if (!b.cap && (e = cudaStreamCreateWithFlags(&b.cap, cudaStreamNonBlocking)) != cudaSuccess)
         return stf_cuda_fail(e, "capture stream");
+    for (int i = 0; i < kBranches; ++i) {
+        if (!b.branch[i] && (e = cudaStreamCreateWithFlags(&b.branch[i], cudaStreamNonBlocking)) != cudaSuccess)
+            return stf_cuda_fail(e, "branch stream");
+        if (!b.join[i] && (e = cudaEventCreateWithFlags(&b.join[i], cudaEventDisableTiming)) != cudaSuccess)
+            return stf_cuda_fail(e, "event");
+    }
+    if (!b.fork && (e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming)) != cudaSuccess)
+        return stf_cuda_fail(e, "event");
     for (int k = 0; k < 2; ++k)
         if (!b.done[k] && (e = cudaEventCreateWithFlags(&b.done[k], cudaEventDisableTiming)) != cudaSuccess)
             return stf_cuda_fail(e, "event");
-    if (bytes <= b.cap_bytes && groups <= b.cap_groups) return STF_OK;
+    if (bytes <= b.cap_bytes && counters <= b.cap_counters) return STF_OK;
     for (int k = 0; k < 2; ++k) {
         if (b.used[k]) cudaEventSynchronize(b.done[k]);
         if (b.host[k]) cudaFreeHost(b.host[k]);
@@ -177,30 +204,30 @@ stf_status ensure_buffers(size_t bytes, int groups)
     }
     b.cap_bytes = 0;
     const size_t nb = std::max(bytes * 2, (size_t)65536);
-    const int ng = std::max(groups, 8);
+    const int nc = std::max(counters * 2, 64);
     for (int k = 0; k < 2; ++k) {
         if ((e = cudaMallocHost(&b.host[k], nb)) != cudaSuccess || (e = cudaMalloc(&b.dev[k], nb)) != cudaSuccess ||
-            (e = cudaMalloc(&b.counters[k], ng * sizeof(int))) != cudaSuccess)
+            (e = cudaMalloc(&b.counters[k], nc * sizeof(int))) != cudaSuccess)
             return stf_cuda_fail(e, "batch buffers");
     }
     b.cap_bytes = nb;
-    b.cap_groups = ng;
+    b.cap_counters = nc;
     return STF_OK;
 }
 
-// Views grouped by material kind, costliest first; items cut per view.
-void build_groups(const stf_view* views, int n, int filter, int mode, std::vector<Group>& groups, std::vector<int>& sched)
+// Views grouped by material kind (at most kBatchMaxViews per group), costliest first; items cut
+// per view and collected per variant.
+void build_groups(const stf_view* views, int n, int filter, int mode, std::vector<Group>& groups)
 {
     std::map<int, int> gi;
     std::vector<double> cost(n);
-    sched.assign(n, kDefaultSchedule);
     for (int i = 0; i < n; ++i) {
         const int f = view_filter(views[i], filter);
         cost[i] = (double)views[i].width * views[i].height * (f == STF_FILTER_BSPLINE3 ? 1.5 : 1.0);
         const int k = views[i].tex->kind;
-        if (!gi.count(k)) {
+        if (!gi.count(k) || (int)groups[gi[k]].views.size() == kBatchMaxViews) {
             gi[k] = (int)groups.size();
-            groups.push_back(Group{k, {}, {}, 0, 0, 0});
+            groups.push_back(Group{k, {}, {}, 0});
         }
         groups[gi[k]].views.push_back(i);
     }
@@ -210,11 +237,17 @@ void build_groups(const stf_view* views, int n, int filter, int mode, std::vecto
             const stf_view& v = views[g.views[local]];
             int tw, th, sc;
             resolve(v, filter, mode, &tw, &th, &sc);
-            sched[g.views[local]] = sc;
             const int tiles = ((v.width + tw - 1) / tw) * ((v.height + th - 1) / th);
             const int per = kWarpsPerBlock * sc;
             const int variant = view_filter(v, filter) * 3 + tile_code(tw, th);
-            for (int t0 = 0; t0 < tiles; t0 += per) g.items.push_back(WorkItem{local, t0, std::min(per, tiles - t0), variant});
+            Sub* sub = nullptr;
+            for (Sub& x : g.subs)
+                if (x.variant == variant) sub = &x;
+            if (!sub) {
+                g.subs.push_back(Sub{variant, {}, 0, 0, 0});
+                sub = &g.subs.back();
+            }
+            for (int t0 = 0; t0 < tiles; t0 += per) sub->items.push_back(WorkItem{local, t0, std::min(per, tiles - t0), variant});
         }
     }
 }
@@ -225,25 +258,29 @@ stf_status render_batch_impl(const stf_view* views, int n, int filter, int mode,
     stf_status st = stf_device_state(nullptr, &lut);
     if (st != STF_OK) return st;
     std::vector<Group> groups;
-    std::vector<int> sched;
-    build_groups(views, n, filter, mode, groups, sched);
-    // staging layout: per group [DevView x views][WorkItem x items], 256-byte aligned sections
+    build_groups(views, n, filter, mode, groups);
+    // staging layout: per group [DevView x views] then [WorkItem x items] per variant, 256-byte aligned
     size_t off = 0;
+    int ncounters = 0;
     std::string shape = "m" + std::to_string(mode);
     for (Group& g : groups) {
         g.views_off = off;
         off += ((g.views.size() * sizeof(DevView) + 255) / 256) * 256;
-        g.items_off = off;
-        off += ((g.items.size() * sizeof(WorkItem) + 255) / 256) * 256;
-        int per_sm = 0;
-        cudaError_t e = launch_batch(g.kind, nullptr, nullptr, 0, nullptr, 0, mode, &per_sm, nullptr);
-        if (e != cudaSuccess) return stf_cuda_fail(e, "occupancy query");
-        g.grid = std::max(1, std::min(per_sm, 8)) * sm_count();
-        g.grid = std::min<long long>(g.grid, (long long)g.items.size());
-        shape += "|k" + std::to_string(g.kind) + "v" + std::to_string(g.views.size()) + "i" + std::to_string(g.items.size()) +
-                 "g" + std::to_string(g.grid);
+        shape += "|k" + std::to_string(g.kind) + "v" + std::to_string(g.views.size());
+        for (Sub& sub : g.subs) {
+            sub.items_off = off;
+            off += ((sub.items.size() * sizeof(WorkItem) + 255) / 256) * 256;
+            int per_sm = 0;
+            cudaError_t e = launch_batch(g.kind, nullptr, 0, nullptr, 0, mode, sub.variant, &per_sm, nullptr);
+            if (e != cudaSuccess) return stf_cuda_fail(e, "occupancy query");
+            sub.grid = (int)std::min<long long>((long long)std::max(1, std::min(per_sm, 8)) * sm_count(),
+                                                (long long)sub.items.size());
+            sub.counter = ncounters++;
+            shape += "/x" + std::to_string(sub.variant) + "i" + std::to_string(sub.items.size()) + "g" +
+                     std::to_string(sub.grid);
+        }
     }
-    if ((st = ensure_buffers(off, (int)groups.size())) != STF_OK) return st;
+    if ((st = ensure_buffers(off, ncounters)) != STF_OK) return st;
     BatchState& b = g_batch;
     const int k = b.next;
     b.next ^= 1;
@@ -253,29 +290,41 @@ stf_status render_batch_impl(const stf_view* views, int n, int filter, int mode,
     }
     for (const Group& g : groups) {
         DevView* dv = reinterpret_cast<DevView*>(b.host[k] + g.views_off);
-        for (size_t i = 0; i < g.views.size(); ++i) stf_fill_devview(views[g.views[i]], filter, mode, seed, lut, dv[i]);
-        // the tile shape the items were cut for
         for (size_t i = 0; i < g.views.size(); ++i) {
+            const stf_view& v = views[g.views[i]];
+            stf_fill_devview(v, filter, mode, seed, lut, dv[i]);
             int tw, th, sc;
-            resolve(views[g.views[i]], filter, mode, &tw, &th, &sc);
+            resolve(v, filter, mode, &tw, &th, &sc);  // the tile shape the items were cut for
             dv[i].tile_w = tw;
             dv[i].tile_h = th;
             dv[i].tiles_x = (dv[i].width + tw - 1) / tw;
             dv[i].tiles_y = (dv[i].height + th - 1) / th;
         }
-        memcpy(b.host[k] + g.items_off, g.items.data(), g.items.size() * sizeof(WorkItem));
+        for (const Sub& sub : g.subs)
+            memcpy(b.host[k] + sub.items_off, sub.items.data(), sub.items.size() * sizeof(WorkItem));
     }
     cudaStream_t user = stf_stream();
     cudaError_t e;
+    // copy, counter reset, then per group: its views into the kind's constant bank and its variant
+    // kernels as concurrent branches (a variant's tail overlaps the next one's start)
     auto enqueue = [&](cudaStream_t s) -> cudaError_t {
         cudaError_t r = cudaMemcpyAsync(b.dev[k], b.host[k], off, cudaMemcpyHostToDevice, s);
-        if (r == cudaSuccess) r = cudaMemsetAsync(b.counters[k], 0, groups.size() * sizeof(int), s);
+        if (r == cudaSuccess) r = cudaMemsetAsync(b.counters[k], 0, ncounters * sizeof(int), s);
         for (size_t gi = 0; gi < groups.size() && r == cudaSuccess; ++gi) {
             const Group& g = groups[gi];
-            int unused = 0;
-            r = launch_batch(g.kind, reinterpret_cast<const DevView*>(b.dev[k] + g.views_off),
-                             reinterpret_cast<const WorkItem*>(b.dev[k] + g.items_off), (int)g.items.size(),
-                             b.counters[k] + gi, g.grid, mode, &unused, s);
+            r = set_views(g.kind, reinterpret_cast<const DevView*>(b.dev[k] + g.views_off), (int)g.views.size(), s);
+            if (r == cudaSuccess) r = cudaEventRecord(b.fork, s);
+            for (size_t j = 0; j < g.subs.size() && r == cudaSuccess; ++j) {
+                const Sub& sub = g.subs[j];
+                cudaStream_t bs = b.branch[j % kBranches];
+                int unused = 0;
+                r = cudaStreamWaitEvent(bs, b.fork, 0);
+                if (r == cudaSuccess)
+                    r = launch_batch(g.kind, reinterpret_cast<const WorkItem*>(b.dev[k] + sub.items_off), (int)sub.items.size(),
+                                     b.counters[k] + sub.counter, sub.grid, mode, sub.variant, &unused, bs);
+                if (r == cudaSuccess) r = cudaEventRecord(b.join[j % kBranches], bs);
+                if (r == cudaSuccess) r = cudaStreamWaitEvent(s, b.join[j % kBranches], 0);
+            }
         }
         return r;
     };

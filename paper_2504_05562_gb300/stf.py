@@ -54,7 +54,7 @@ EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_str
            "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy", "stf_set_option", "stf_get_stat",
            "stf_autotune", "stf_view_config", "stf_autotune_save", "stf_autotune_load", "stf_autotune_clear",
            "stf_render_views_noalloc")
-NOALLOC_MAX_VIEWS, NOALLOC_MAX_ITEMS = 256, 262144
+NOALLOC_MAX_VIEWS, NOALLOC_MAX_ITEMS = 224, 262144
 OPT_BATCH_GRAPHS = 1
 STAT_GRAPH_BUILDS, STAT_GRAPH_REPLAYS = 1, 2
 
