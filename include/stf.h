@@ -191,7 +191,8 @@ stf_status stf_autotune_clear(void);
  * fixed __device__ array of about 4.2 MB inside the library, held by every GPU that loads it
  * until the process exits. Inputs (textures, created beforehand) and outputs stay the caller's.
  * Limits: at most STF_NOALLOC_MAX_VIEWS views per call (more -> STF_ERR_INVALID_ARG, nothing
- * enqueued); work items are coarsened to fit STF_NOALLOC_MAX_ITEMS, which changes no pixel.
+ * enqueued); work items are coarsened to fit STF_NOALLOC_MAX_ITEMS, which changes no pixel;
+ * neural-texture views of one call must share one decoder (else STF_ERR_INVALID_ARG).
  * The first call on a device looks up the array's device address and uploads a 1 KB table with
  * a blocking copy: make it before any stream capture. All calls share the array (the counters
  * are cleared on each call): calls that overlap on the GPU race. Asynchronous on the library

@@ -2,6 +2,7 @@
 // dispatch of the render kernels. Declarations and the contract are in include/stf.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -45,6 +46,33 @@ extern "C" stf_status stf_set_stream(void* s)
 {
     g_stream = (cudaStream_t)s;
     return STF_OK;
+}
+
+// ------------------------------------------------------------------------------ occupancy
+
+// Resident blocks per SM of a kernel, counted from its registers, shared memory and threads (and
+// at most four, the blocks whose 128 tensor-memory columns fit in an SM's 512). The runtime's
+// occupancy query reports one block for kernels that allocate tensor memory, which would leave
+// the persistent decode-pipeline grids at half the SMs' capacity.
+cudaError_t stf_resident_blocks(const void* kernel, int threads, int dyn_bytes, int* n)
+{
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, regs_sm = 0, thr_sm = 0, reserved = 0;
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess || (e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess)
+        return e;
+    const int warps = (threads + 31) / 32;
+    const int regs_block = warps * ((fa.numRegs * 32 + 255) / 256) * 256;  // allocated per warp in 256s
+    const int smem_block = (int)fa.sharedSizeBytes + dyn_bytes + reserved;
+    int b = regs_block > 0 ? regs_sm / regs_block : 1;
+    b = std::min(b, smem_sm / std::max(smem_block, 1));
+    b = std::min(b, thr_sm / std::max(threads, 1));
+    *n = std::max(1, std::min(b, 4));
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------------------ per-device state
@@ -367,6 +395,7 @@ void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long lon
     d.ch_ao = v.ch_ao;
     d.c_true = t->channels;
     d.neural = t->decoder_params;
+    stf_device_state(&d.flags, nullptr);
     d.affine = (v.H[6] == 0.0f && v.H[7] == 0.0f && v.H[8] == 1.0f) ? 1 : 0;
     if (!v.shading) d.shade_layout = 0;
     else if (v.ch_albedo == 0 && v.ch_normal == 3 && v.ch_rough == 5 && v.ch_ao == 6) d.shade_layout = 1;

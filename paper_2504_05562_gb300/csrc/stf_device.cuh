@@ -64,6 +64,7 @@ struct DevView {
     int filter, tile_w, tile_h;
     int affine;               // H[6] == H[7] == 0 and H[8] == 1: hw == 1 exactly, no division needed
     const void* neural;       // decoder parameters for K_NEURAL
+    int* flags;               // device error counters: [0] timed-out waits
 };
 
 // A run of tiles of one view for the persistent multi-view kernel. variant = filter * 3 + tile

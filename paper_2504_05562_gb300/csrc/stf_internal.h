@@ -33,6 +33,9 @@ stf_status stf_render_batch(const stf_view* views, int n, int filter, int mode, 
 // tile shape and schedule of a view, as the multi-view scheduler resolves them (no heap use)
 void stf_resolve_view_config_nohalloc(const stf_view& v, int filter, int mode, int* tw, int* th, int* sched);
 
+// resident blocks per SM, counted from the kernel's resources (stf_api.cu)
+cudaError_t stf_resident_blocks(const void* kernel, int threads, int dyn_bytes, int* n);
+
 // neural decoder (stf_neural.cu)
 stf_status stf_create_neural_texture(const stf_texture_desc* d, stf_texture** out);
 cudaError_t stf_launch_neural_view(const stf::DevView& d, int mode, cudaStream_t s);

@@ -1,42 +1,34 @@
-// Render kernels. One warp renders one TW x TH pixel tile (lane = ly * TW + lx), which is the
-// paper's wave-to-pixel mapping with linear row lane order (Section 2.3, Figure "wave"); texels
-// are exchanged with __shfl_sync, the CUDA counterpart of WaveReadLaneAt (Section 4.5).
+// Render kernels of the stored material kinds. One warp renders one TW x TH pixel tile
+// (lane = ly * TW + lx), which is the paper's wave-to-pixel mapping with linear row lane order
+// (Section 2.3, Figure "wave"); texels are exchanged through per-warp shared-memory records, the
+// CUDA counterpart of WaveReadLaneAt (Section 4.5). The neural kind has its own kernels
+// (stf_nn_render.cuh).
 #pragma once
 
 #include <float.h>
 
 #include "stf_device.cuh"
-#include "stf_neural.cuh"
 
 namespace stf {
 
 constexpr unsigned kFull = 0xffffffffu;
 
 template <int KIND> struct Channels { static constexpr int C = Mat<KIND>::C; };
-template <> struct Channels<K_NEURAL> { static constexpr int C = 8; };
 
-// Fetch or decode one texel of lattice point (x, y) with clamp-to-edge addressing.
-// For K_NEURAL all 32 lanes must call it together (the decode is a warp-wide matrix product).
+// Fetch one texel of lattice point (x, y) with clamp-to-edge addressing.
 template <int KIND>
-__device__ __forceinline__ void fetch_texel(const DevView& v, int x, int y, float (&t)[Channels<KIND>::C],
-                                            unsigned char* scratch)
+__device__ __forceinline__ void fetch_texel(const DevView& v, int x, int y, float (&t)[Channels<KIND>::C])
 {
     x = clampi(x, 0, v.tex_w - 1);
     y = clampi(y, 0, v.tex_h - 1);
-    if constexpr (KIND == K_NEURAL) nn_decode_warp(reinterpret_cast<const NeuralDev*>(v.neural), x, y, t, scratch);
-    else Mat<KIND>::fetch(v, x, y, t);
+    Mat<KIND>::fetch(v, x, y, t);
 }
-
-// Per-warp shared scratch the texel decode needs (the neural decoder's A tile).
-template <int KIND> struct DecodeScratch { static constexpr int bytes = 16; };
-template <> struct DecodeScratch<K_NEURAL> { static constexpr int bytes = kNnWarpSmem; };
 
 // One warp tile of one view. MODE: 0 full filter, 1 one-tap, 2 quad 2x2, 3..5 wave k x k.
 // All 32 lanes execute every shuffle (off-screen lanes of a partial tile compute with
 // extrapolated coordinates and only skip the store).
 template <int KIND, int F, int MODE, int TW, int TH>
-__device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane, float4* rec, float* wtab,
-                                            unsigned char* scratch)
+__device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane, float4* rec, float* wtab)
 {
     constexpr int C = Channels<KIND>::C;
     const int lx = lane % TW, ly = lane / TW;
@@ -55,15 +47,13 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
         axis_weights<F>(cy, ay);
 #pragma unroll
         for (int c = 0; c < C; ++c) res[c] = 0.0f;
-        // a neural decode is a warp-wide tensor-core product: keep one row of taps in flight
-        constexpr int kRowUnroll = KIND == K_NEURAL ? 1 : Taps<F>::N;
-#pragma unroll kRowUnroll
+#pragma unroll
         for (int s = 0; s < Taps<F>::N; ++s) {
 #pragma unroll
             for (int t = 0; t < Taps<F>::N; ++t) {
                 const float wt = __fmul_rn(ax.w[t], ay.w[s]);
                 float T[C];
-                fetch_texel<KIND>(v, ax.base + t, ay.base + s, T, scratch);
+                fetch_texel<KIND>(v, ax.base + t, ay.base + s, T);
 #pragma unroll
                 for (int c = 0; c < C; ++c) res[c] = fmaf(wt, T[c], res[c]);
             }
@@ -79,7 +69,7 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
         axis_select<F>(cy, uy, ay);
         const float p = __fmul_rn(ax.p, ay.p);
         float T[C];
-        fetch_texel<KIND>(v, ax.n, ay.n, T, scratch);
+        fetch_texel<KIND>(v, ax.n, ay.n, T);
         pk = pack_idx(ax.n, ay.n);
         if constexpr (MODE == 1) {
 #pragma unroll
@@ -171,22 +161,19 @@ constexpr int kRecPerLane = 3;
 
 // Blocks resident per SM the kernel is compiled for (caps registers per thread at 65536 /
 // (256 n)): five 8-warp blocks (<= 51 registers) keep the issue-bound texture kinds at 40 warps
-// per SM; the register-heavy neural decode gets two (<= 128 registers).
-template <int KIND> struct MinBlocks { static constexpr int n = 5; };
-template <> struct MinBlocks<K_NEURAL> { static constexpr int n = 2; };
+// per SM.
+constexpr int kMinBlocks = 5;
 
 // One view: block (bx, by) holds 8 warps on tile row by, tiles bx * 8 .. bx * 8 + 7.
 template <int KIND, int F, int MODE, int TW, int TH>
-__global__ void __launch_bounds__(256, MinBlocks<KIND>::n) k_render_view(const DevView v)
+__global__ void __launch_bounds__(256, kMinBlocks) k_render_view(const DevView v)
 {
     __shared__ float4 recs[kWarpsPerBlock * 32 * kRecPerLane];
     __shared__ float wtabs[kWarpsPerBlock * 32 * 8];
-    __shared__ __align__(16) unsigned char scratch[kWarpsPerBlock * DecodeScratch<KIND>::bytes];
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = blockIdx.x * kWarpsPerBlock + warp;
     if (tx >= v.tiles_x) return;  // warp-uniform
-    render_tile<KIND, F, MODE, TW, TH>(v, tx, blockIdx.y, threadIdx.x & 31, recs + warp * 32 * kRecPerLane,
-                                       wtabs + warp * 32 * 8, scratch + warp * DecodeScratch<KIND>::bytes);
+    render_tile<KIND, F, MODE, TW, TH>(v, tx, blockIdx.y, lane, recs + warp * 32 * kRecPerLane, wtabs + warp * 32 * 8);
 }
 
 }  // namespace stf

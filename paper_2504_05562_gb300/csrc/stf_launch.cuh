@@ -6,15 +6,54 @@
 #include <cuda_runtime.h>
 
 #include "stf_kernels.cuh"
+#include "stf_nn_render.cuh"
+#include "stf_internal.h"
 
 namespace stf {
+
+// Opts a kernel into its dynamic shared memory (once: `cached` is the caller's per-instance
+// static) and returns its resident blocks per SM for `threads`-thread blocks.
+template <class K>
+static cudaError_t prepare_dynamic(K kernel, int dyn_bytes, int threads, int& cached, int* per_sm)
+{
+    if (!cached) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_bytes);
+        // the largest shared-memory carve-out, so that every block the registers allow fits
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        e = stf_resident_blocks(reinterpret_cast<const void*>(kernel), threads, dyn_bytes, &cached);
+        if (e != cudaSuccess) return e;
+        if (cached < 1) cached = 1;
+    }
+    *per_sm = cached;
+    return cudaSuccess;
+}
+
+static int device_sms()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
 
 template <int KIND, int F, int MODE, int TW, int TH>
 static cudaError_t launch_one(const DevView& v, cudaStream_t s)
 {
     const dim3 grid((unsigned)((v.tiles_x + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)v.tiles_y);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-    k_render_view<KIND, F, MODE, TW, TH><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
+    if constexpr (KIND == K_NEURAL) {  // persistent decode-pipeline blocks over the 8-tile groups
+        static int cached = 0;
+        int per_sm = 1;
+        constexpr int dyn = (int)sizeof(NnPipeSmem);
+        cudaError_t e = prepare_dynamic(k_render_neural<F, MODE, TW, TH>, dyn, kNnPipeThreads, cached, &per_sm);
+        if (e != cudaSuccess) return e;
+        const long long groups = (long long)grid.x * grid.y;
+        const unsigned blocks = (unsigned)(groups < (long long)per_sm * device_sms() ? groups : (long long)per_sm * device_sms());
+        k_render_neural<F, MODE, TW, TH><<<blocks, kNnPipeThreads, dyn, s>>>(v);
+    } else {
+        k_render_view<KIND, F, MODE, TW, TH><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
+    }
     return cudaGetLastError();
 }
 
@@ -59,14 +98,15 @@ static __constant__ DevView c_batch_views[kBatchMaxViews];
 // on another block, so no wait can stall. One kernel per variant keeps the code of a launch as
 // small as a single-view kernel's.
 template <int KIND, int MODE, int F, int TW, int TH>
-__global__ void __launch_bounds__(256, MinBlocks<KIND>::n)
+__global__ void __launch_bounds__(256, kMinBlocks)
     k_render_batch(const WorkItem* __restrict__ items, int n_items, int* counter)
 {
     __shared__ float4 recs[kWarpsPerBlock * 32 * kRecPerLane];
     __shared__ float wtabs[kWarpsPerBlock * 32 * 8];
-    __shared__ __align__(16) unsigned char scratch[kWarpsPerBlock * DecodeScratch<KIND>::bytes];
     __shared__ WorkItem sw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* rec = recs + warp * 32 * kRecPerLane;
+    float* wtab = wtabs + warp * 32 * 8;
     for (;;) {
         if (threadIdx.x == 0) {
             const int it = atomicAdd(counter, 1);
@@ -77,21 +117,79 @@ __global__ void __launch_bounds__(256, MinBlocks<KIND>::n)
         __syncthreads();  // sw is rewritten by the next pull
         if (w.view < 0) break;
         const DevView& v = c_batch_views[w.view];
-        for (int t = w.tile0 + warp; t < w.tile0 + w.ntiles; t += kWarpsPerBlock) {
+        for (int k = warp; k < w.ntiles; k += kWarpsPerBlock) {
+            const int t = w.tile0 + k;
             const int ty = t / v.tiles_x;
-            render_tile<KIND, F, MODE, TW, TH>(v, t - ty * v.tiles_x, ty, lane, recs + warp * 32 * kRecPerLane,
-                                               wtabs + warp * 32 * 8, scratch + warp * DecodeScratch<KIND>::bytes);
+            render_tile<KIND, F, MODE, TW, TH>(v, t - ty * v.tiles_x, ty, lane, rec, wtab);
         }
     }
+}
+
+struct NnConstViews {
+    __device__ __forceinline__ const DevView& operator()(int i) const { return c_batch_views[i]; }
+};
+
+// The neural kind's multi-view kernel: the same work items, rendered by the 8 client warps of the
+// decode pipeline (all of a batch's neural views share one decoder; view 0 names it). The client
+// warps pull items together (named barrier 1), so every client takes the same rounds.
+template <int MODE, int F, int TW, int TH>
+__global__ void __launch_bounds__(kNnPipeThreads, 2)
+    k_render_neural_batch(const WorkItem* __restrict__ items, int n_items, int* counter)
+{
+    extern __shared__ __align__(128) unsigned char dyn[];
+    __shared__ float wtabs[kNnWtabFloats];
+    __shared__ WorkItem sw;
+    NnPipeSmem& sm = *reinterpret_cast<NnPipeSmem*>(dyn);
+    nn_pipe_setup(sm, reinterpret_cast<const NeuralDev*>(c_batch_views[0].neural));
+    if (threadIdx.x >= kNnRows) {
+        nn_decode_role(sm, c_batch_views[0].flags);
+    } else {
+        const int warp = threadIdx.x >> 5;
+        NnRenderClient<F, MODE, TW, TH, NnConstViews> cl(sm, wtabs + warp * 256, NnConstViews{}, c_batch_views[0].flags);
+#pragma unroll 1
+        for (;;) {
+            if (threadIdx.x == 0) {
+                const int it = atomicAdd(counter, 1);
+                sw = it < n_items ? items[it] : WorkItem{-1, 0, 0, 0};
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            const WorkItem w = sw;
+            asm volatile("bar.sync 1, 256;" ::: "memory");  // sw is rewritten by the next pull
+            if (w.view < 0) break;
+            const DevView& v = c_batch_views[w.view];
+            const int groups = (w.ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+#pragma unroll 1
+            for (int k = 0; k < groups; ++k) {
+                const int j = k * kWarpsPerBlock + warp;
+                const bool active = j < w.ntiles;
+                const int t = w.tile0 + (active ? j : 0);
+                const int ty = t / v.tiles_x;
+                cl.group(w.view, active, t - ty * v.tiles_x, ty);
+            }
+        }
+        cl.finish();
+    }
+    nn_pipe_teardown(sm);
 }
 
 // grid > 0 launches; grid == 0 only reports the instance's resident blocks per SM in *per_sm.
 template <int KIND, int MODE, int F, int TW, int TH>
 static cudaError_t launch_batch_v(const WorkItem* items, int n_items, int* counter, int grid, int* per_sm, cudaStream_t s)
 {
-    if (grid == 0)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE, F, TW, TH>, 256, 0);
-    k_render_batch<KIND, MODE, F, TW, TH><<<grid, 256, 0, s>>>(items, n_items, counter);
+    if constexpr (KIND == K_NEURAL) {
+        static int cached = 0;
+        constexpr int dyn = (int)sizeof(NnPipeSmem);
+        int n = 0;
+        cudaError_t e = prepare_dynamic(k_render_neural_batch<MODE, F, TW, TH>, dyn, kNnPipeThreads, cached, &n);
+        if (e != cudaSuccess || grid == 0) {
+            *per_sm = n;
+            return e;
+        }
+        k_render_neural_batch<MODE, F, TW, TH><<<grid, kNnPipeThreads, dyn, s>>>(items, n_items, counter);
+    } else {
+        if (grid == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE, F, TW, TH>, 256, 0);
+        k_render_batch<KIND, MODE, F, TW, TH><<<grid, 256, 0, s>>>(items, n_items, counter);
+    }
     return cudaGetLastError();
 }
 

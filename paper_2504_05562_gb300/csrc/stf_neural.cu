@@ -291,49 +291,73 @@ __global__ void k_nn_latent_update(float* lat, float* m, float* v, unsigned long
     lat[i] -= lr * (mm * c1) / (sqrtf(vv * c2) + eps);
 }
 
-// Inference copy: FP16 latents, FP16 B fragments of the weights, FP32 biases.
-__global__ void k_nn_export(const float* P, const float* lat, long long nlat, __half* lat16, uint2* wfrag, float* bias)
+// Inference copy: FP16 latents and the three layers as tensor-core B operand images, each bias
+// in two extra K columns (FP16 high part and the FP16 rounding of the remainder).
+__global__ void k_nn_export(const float* P, const float* lat, long long nlat, __half* lat16, __half* wimg)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nlat) lat16[i] = __float2half_rn(lat[i]);
-    if (i < kNnFrags * 32) {
-        const int f = (int)(i / 32), lane = (int)(i % 32);
-        const int g = lane >> 2, t = lane & 3;
-        const float* Wm;
-        int nin, kt, nt;
-        if (f < 16) { Wm = P + oW1; nin = kNnIn; kt = f / 8; nt = f % 8; }
-        else if (f < 48) { Wm = P + oW2; nin = kNnH; kt = (f - 16) / 8; nt = (f - 16) % 8; }
-        else { Wm = P + oW3; nin = kNnH; kt = f - 48; nt = 0; }
-        const int n = nt * 8 + g;
-        float w[4];
-        const int ks[4] = {kt * 16 + 2 * t, kt * 16 + 2 * t + 1, kt * 16 + 8 + 2 * t, kt * 16 + 9 + 2 * t};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) w[q] = ks[q] < nin ? Wm[n * nin + ks[q]] : 0.0f;
-        wfrag[i] = make_uint2(pack_h2(w[0], w[1]), pack_h2(w[2], w[3]));
-    }
-    if (i < 2 * kNnH + kNnOut) {
-        const int j = (int)i;
-        bias[j] = j < kNnH ? P[ob1 + j] : (j < 2 * kNnH ? P[ob2 + j - kNnH] : P[ob3 + j - 2 * kNnH]);
+    constexpr int n1 = 64 * kNnK1, n2 = 64 * kNnK2, n3 = 16 * kNnK2;
+    if (i < n1 + n2 + n3) {
+        int j = (int)i, r, k, K, base, nin, rows;
+        const float *Wm, *bv;
+        if (j < n1) { K = kNnK1; base = 0; Wm = P + oW1; bv = P + ob1; nin = kNnIn; rows = kNnH; }
+        else if (j < n1 + n2) { j -= n1; K = kNnK2; base = kNnB1Bytes; Wm = P + oW2; bv = P + ob2; nin = kNnH; rows = kNnH; }
+        else { j -= n1 + n2; K = kNnK2; base = kNnB1Bytes + kNnB2Bytes; Wm = P + oW3; bv = P + ob3; nin = kNnH; rows = kNnOut; }
+        r = j / K;
+        k = j % K;
+        __half val = __float2half_rn(0.0f);
+        if (r < rows) {
+            if (k < nin) val = __float2half_rn(Wm[r * nin + k]);
+            else if (k == nin) val = __float2half_rn(bv[r]);
+            else if (k == nin + 1) val = __float2half_rn(bv[r] - __half2float(__float2half_rn(bv[r])));
+        }
+        wimg[(base + (r / 8) * (K / 8) * 128 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2) / 2] = val;
     }
 }
 
-// Decodes a list of texels (packed ix | iy << 16) with the inference kernel; 8 warps per block,
-// 32 texels per warp (the tail warp repeats its last texel and skips the extra stores).
-__global__ void __launch_bounds__(256) k_nn_decode_list(const NeuralDev* nd, const int* idx, int n, int W, int H, float* out)
+// Decodes a list of texels (packed ix | iy << 16) through the decode pipeline: persistent blocks,
+// 256 texels per round (a tail round decodes fewer rows).
+__global__ void __launch_bounds__(kNnPipeThreads, 2) k_nn_decode_list(const NeuralDev* nd, const int* idx, int n, int W,
+                                                                      int H, float* out, int* flags)
 {
-    __shared__ __align__(16) unsigned char scratch[8 * kNnWarpSmem];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int base = (blockIdx.x * 8 + warp) * 32;
-    if (base >= n) return;  // warp-uniform
-    const int i = min(base + lane, n - 1);
-    const int x = clampi(idx[i] & 0xffff, 0, W - 1), y = clampi(idx[i] >> 16, 0, H - 1);
-    float t[8];
-    nn_decode_warp(nd, x, y, t, scratch + warp * kNnWarpSmem);
-    if (base + lane < n) {
-        float4* o = reinterpret_cast<float4*>(out + (size_t)(base + lane) * 8);
-        o[0] = make_float4(t[0], t[1], t[2], t[3]);
-        o[1] = make_float4(t[4], t[5], t[6], t[7]);
+    extern __shared__ __align__(128) unsigned char dyn[];
+    NnPipeSmem& sm = *reinterpret_cast<NnPipeSmem*>(dyn);
+    nn_pipe_setup(sm, nd);
+    if (threadIdx.x >= kNnRows) {
+        nn_decode_role(sm, flags);
+    } else {
+        const int row = threadIdx.x;
+        NnWaiter w{flags, 0};
+        uint32_t r = 0;
+        int prev = -1;
+#pragma unroll 1
+        for (int base = blockIdx.x * kNnRows;; base += gridDim.x * kNnRows) {
+            const bool more = base < n;
+            const int i = base + row;
+            if (more && i < n) {
+                uint32_t in[12];
+                nn_inputs(*nd, clampi(idx[i] & 0xffff, 0, W - 1), clampi(idx[i] >> 16, 0, H - 1), in);
+                nn_put_inputs(sm, r & 1, row, in);
+            }
+            nn_publish(sm, r & 1, more ? 1 : 0);
+            if (prev >= 0) {
+                const uint32_t q = r - 1;
+                w.wait(sm.out_full[q & 1], (q >> 1) & 1u);
+                if (prev + row < n) {
+                    float t[8];
+                    nn_get_outputs(sm, q & 1, row, t);
+                    float4* o = reinterpret_cast<float4*>(out + (size_t)(prev + row) * 8);
+                    o[0] = make_float4(t[0], t[1], t[2], t[3]);
+                    o[1] = make_float4(t[4], t[5], t[6], t[7]);
+                }
+            }
+            if (!more) break;
+            prev = base;
+            ++r;
+        }
     }
+    nn_pipe_teardown(sm);
 }
 
 uint32_t crc32(const unsigned char* p, size_t n, uint32_t crc = 0)
@@ -357,8 +381,7 @@ struct stf_decoder {
     float *lat = nullptr, *latm = nullptr, *latv = nullptr;
     unsigned long long* lat_acc = nullptr;
     __half* lat16 = nullptr;
-    uint2* wfrag = nullptr;
-    float* bias = nullptr;
+    __half* wimg = nullptr;
     NeuralDev* dev = nullptr;  // device copy of the inference parameter block
     float feat[16][4];         // FP32 phase features (training)
     // per-batch scratch
@@ -375,7 +398,7 @@ template <class T> cudaError_t dalloc(T** p, size_t count) { return cudaMalloc((
 
 void dfree(stf_decoder* d)
 {
-    void* ps[] = {d->P, d->Pm, d->Pv, d->lat, d->latm, d->latv, d->lat_acc, d->lat16, d->wfrag, d->bias, d->dev,
+    void* ps[] = {d->P, d->Pm, d->Pv, d->lat, d->latm, d->latv, d->lat_acc, d->lat16, d->wimg, d->dev,
                   d->idx, d->part, d->loss_part, d->loss};
     for (void* p : ps)
         if (p) cudaFree(p);
@@ -405,8 +428,8 @@ stf_status alloc_decoder(stf_decoder* d)
     const long long nl = d->nlat;
     if ((e = dalloc(&d->P, kNnParams)) || (e = dalloc(&d->Pm, kNnParams)) || (e = dalloc(&d->Pv, kNnParams)) ||
         (e = dalloc(&d->lat, nl)) || (e = dalloc(&d->latm, nl)) || (e = dalloc(&d->latv, nl)) ||
-        (e = dalloc(&d->lat_acc, nl)) || (e = dalloc(&d->lat16, nl)) || (e = dalloc(&d->wfrag, kNnFrags * 32)) ||
-        (e = dalloc(&d->bias, 2 * kNnH + kNnOut)) || (e = dalloc(&d->dev, 1)) || (e = dalloc(&d->loss, 1)))
+        (e = dalloc(&d->lat_acc, nl)) || (e = dalloc(&d->lat16, nl)) || (e = dalloc(&d->wimg, kNnImgBytes / 2)) ||
+        (e = dalloc(&d->dev, 1)) || (e = dalloc(&d->loss, 1)))
         return stf_cuda_fail(e, "decoder allocation");
     cudaMemset(d->Pm, 0, kNnParams * 4);
     cudaMemset(d->Pv, 0, kNnParams * 4);
@@ -425,8 +448,7 @@ stf_status alloc_decoder(stf_decoder* d)
         h.feat[p] = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
     }
     h.lat16 = reinterpret_cast<const uint4*>(d->lat16);
-    h.wfrag = d->wfrag;
-    h.bias = d->bias;
+    h.wimg = reinterpret_cast<const uint4*>(d->wimg);
     h.gw = d->cfg.latent_w;
     h.gh = d->cfg.latent_h;
     h.rshift = d->rshift;
@@ -451,8 +473,8 @@ stf_status ensure_scratch(stf_decoder* d, int n)
 
 stf_status export_inference(stf_decoder* d, cudaStream_t s)
 {
-    const long long n = d->nlat > kNnFrags * 32 ? d->nlat : kNnFrags * 32;
-    k_nn_export<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d->P, d->lat, d->nlat, d->lat16, d->wfrag, d->bias);
+    const long long n = d->nlat > kNnImgBytes / 2 ? d->nlat : kNnImgBytes / 2;
+    k_nn_export<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d->P, d->lat, d->nlat, d->lat16, d->wimg);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? STF_OK : stf_cuda_fail(e, "export kernel");
 }
@@ -631,9 +653,25 @@ extern "C" stf_status stf_decoder_decode(const stf_decoder* d, const int32_t* te
     if (!d || !texels || !out || n < 0) return stf_fail(STF_ERR_INVALID_ARG, "stf_decoder_decode: bad arguments");
     if (((uintptr_t)out & 15) != 0) return stf_fail(STF_ERR_INVALID_ARG, "out must be 16-byte aligned");
     if (n == 0) return STF_OK;
-    const int warps = (n + 31) / 32;
-    k_nn_decode_list<<<(warps + 7) / 8, 256, 0, stf_stream()>>>(d->dev, texels, n, d->cfg.tex_w, d->cfg.tex_h, out);
-    cudaError_t e = cudaGetLastError();
+    int* flags = nullptr;
+    stf_status st = stf_device_state(&flags, nullptr);
+    if (st != STF_OK) return st;
+    static int per_sm = 0;
+    cudaError_t e = cudaSuccess;
+    if (!per_sm) {
+        e = cudaFuncSetAttribute(k_nn_decode_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(NnPipeSmem));
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_nn_decode_list, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e == cudaSuccess) e = stf_resident_blocks(reinterpret_cast<const void*>(k_nn_decode_list), kNnPipeThreads, (int)sizeof(NnPipeSmem), &per_sm);
+        if (e != cudaSuccess) return stf_cuda_fail(e, "decode kernel set-up");
+        if (per_sm < 1) per_sm = 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int rounds = (n + kNnRows - 1) / kNnRows;
+    const int blocks = rounds < per_sm * sms ? rounds : per_sm * sms;
+    k_nn_decode_list<<<blocks, kNnPipeThreads, sizeof(NnPipeSmem), stf_stream()>>>(d->dev, texels, n, d->cfg.tex_w, d->cfg.tex_h, out, flags);
+    e = cudaGetLastError();
     return e == cudaSuccess ? STF_OK : stf_cuda_fail(e, "decode kernel");
 }
 

@@ -7,12 +7,11 @@
 // costly per-texel decode that stochastic filtering amortises (Sections 1 and 5.7).
 //
 // Inference precision: latents and weights FP16, the 24 inputs and both hidden layers rounded to
-// FP16, products accumulated in FP32 by the tensor cores, biases and outputs FP32.
+// FP16, products and biases accumulated in FP32 by the tensor cores, outputs FP32.
 //
-// A warp decodes the 32 texels its lanes hold at once: the 32 input rows form the A operand of
-// m16n8k16 tensor-core products (two 16-row tiles), the weights are pre-arranged B fragments,
-// and each layer's FP32 accumulators are converted in registers into the next layer's FP16 A
-// fragments (no shared-memory round trip between layers).
+// Decoding runs as a pipeline inside each block: client warps prepare the inputs of 256 texels,
+// a decode warpgroup evaluates the MLP with tcgen05 tensor-core products (see the decode pipeline
+// section below).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -24,19 +23,27 @@ namespace stf {
 
 constexpr int kNnIn = 24, kNnH = 64, kNnOut = 8, kNnLat = 16;
 constexpr int kNnParams = kNnH * kNnIn + kNnH + kNnH * kNnH + kNnH + kNnOut * kNnH + kNnOut;  // 6280
-constexpr int kNnFrags = 16 + 32 + 4;       // B fragments of layers 1, 2, 3
-constexpr int kNnRowBytes = 80;             // A-tile row stride (32 halves + pad, conflict-free ldmatrix)
-constexpr int kNnWarpSmem = 32 * kNnRowBytes;  // 2560 bytes of shared scratch per warp
+
+// tcgen05 operand images (FP16, K-major, no swizzle: element (r, k) of an R x K matrix at byte
+// (r / 8) * (K / 8) * 128 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2, i.e. 8 x 8 core matrices
+// of 128 bytes, K-adjacent ones 128 bytes apart, row groups (K / 8) * 128 bytes apart). Each
+// layer's bias rides in two extra K columns: the weight image holds its FP16 high part hi(b) and
+// the FP16 rounding of b - hi(b), the activation operand holds 1 in both, so the FP32
+// accumulation adds b to within 2^-22 |b| and the epilogue is a plain ReLU.
+constexpr int kNnK1 = 32;                   // layer 1: 24 inputs, bias columns 24 / 25, zeros
+constexpr int kNnK2 = 80;                   // layers 2, 3: 64 hidden, bias columns 64 / 65, zeros
+constexpr int kNnB1Bytes = 64 * kNnK1 * 2;  // W1: N = 64 x K = 32
+constexpr int kNnB2Bytes = 64 * kNnK2 * 2;  // W2: N = 64 x K = 80
+constexpr int kNnB3Bytes = 16 * kNnK2 * 2;  // W3: N = 16 (8 outputs + zero rows) x K = 80
+constexpr int kNnImgBytes = kNnB1Bytes + kNnB2Bytes + kNnB3Bytes;  // 16896
 
 // Device parameter block of a decoder's inference copy.
 struct NeuralDev {
     const uint4* lat16;   // [gh][gw][2]: 16 FP16 latents per cell
-    const uint2* wfrag;   // [kNnFrags][32 lanes]: B fragments (W1 k-tile 0..1 x n-tile 0..7,
-                          // W2 k-tile 0..3 x n-tile 0..7, W3 k-tile 0..3)
-    const float* bias;    // b1[64], b2[64], b3[8]
     int gw, gh, rshift;   // R = 1 << rshift
     float inv_r;          // 1 / R (exact)
     uint2 feat[16];       // phase p: (sin, cos)(2 pi phi) and (sin, cos)(4 pi phi) as half2 pairs
+    const uint4* wimg;    // the three layers (weights and biases) as tensor-core B operands
 };
 
 __device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
@@ -48,22 +55,6 @@ __device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
 __device__ __forceinline__ float2 unpack_h2(uint32_t w)
 {
     return __half22float2(*reinterpret_cast<const __half2*>(&w));
-}
-
-__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint2 b)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
-}
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], uint32_t saddr)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(saddr));
 }
 
 // Bilinear position along one latent axis: lower cell, upper cell (both clamped) and fraction.
@@ -117,88 +108,420 @@ __device__ __forceinline__ void nn_inputs(const NeuralDev& nd, int x, int y, uin
     row[11] = fyw.y;
 }
 
-// Bias-initialised accumulator of an n-tile: columns nt * 8 + 2 (lane % 4) + {0, 1}.
-__device__ __forceinline__ void nn_bias(float (&c)[4], const float* b, int nt, int lane)
+// ------------------------------------------------------------------------------ tcgen05 primitives
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, K-major without swizzle: start address, leading (K) byte
+// offset between core matrices, stride (M/N) byte offset between 8-row groups, version 1.
+__device__ __forceinline__ uint64_t nn_sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    const float2 v = __ldg(reinterpret_cast<const float2*>(b + nt * 8 + 2 * (lane & 3)));
-    c[0] = v.x; c[1] = v.y; c[2] = v.x; c[3] = v.y;
+    return (uint64_t)((addr >> 4) & 0x3fff) | ((uint64_t)((lbo >> 4) & 0x3fff) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fff) << 32) | ((uint64_t)1 << 46);
 }
 
-// ReLU of two n-tiles' accumulators -> the FP16 A fragment of one 16-wide k-tile.
-__device__ __forceinline__ void nn_relu_pack(const float (&lo)[4], const float (&hi)[4], uint32_t (&a)[4])
+// Instruction descriptor of kind::f16: D = F32, A = B = F16, both K-major, N, M = 128.
+__host__ __device__ constexpr uint32_t nn_idesc(int n)
 {
-    a[0] = pack_h2(fmaxf(lo[0], 0.0f), fmaxf(lo[1], 0.0f));
-    a[1] = pack_h2(fmaxf(lo[2], 0.0f), fmaxf(lo[3], 0.0f));
-    a[2] = pack_h2(fmaxf(hi[0], 0.0f), fmaxf(hi[1], 0.0f));
-    a[3] = pack_h2(fmaxf(hi[2], 0.0f), fmaxf(hi[3], 0.0f));
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-// Decodes the texel (x, y) of every lane (all 32 lanes call together). `smem` is this warp's
-// kNnWarpSmem bytes of 16-byte-aligned shared scratch.
-__device__ __forceinline__ void nn_decode_warp(const NeuralDev* ndp, int x, int y, float (&t)[8], unsigned char* smem)
+__device__ __forceinline__ void nn_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum)
 {
-    const NeuralDev& nd = *ndp;
-    const int lane = threadIdx.x & 31;
-    uint32_t row[12];
-    nn_inputs(nd, x, y, row);
-    uint4* my = reinterpret_cast<uint4*>(smem + lane * kNnRowBytes);
-    my[0] = make_uint4(row[0], row[1], row[2], row[3]);
-    my[1] = make_uint4(row[4], row[5], row[6], row[7]);
-    my[2] = make_uint4(row[8], row[9], row[10], row[11]);
-    my[3] = make_uint4(0u, 0u, 0u, 0u);  // inputs 24..31 are zero padding
-    __syncwarp();
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    float out[2][4];
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+// The same product with A read from tensor memory (row m = lane m, K packed two per column).
+__device__ __forceinline__ void nn_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+        :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void nn_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ uint32_t nn_try_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done;
+}
+
+__device__ __forceinline__ void nn_arrive(uint32_t mbar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" :: "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        // layer 1: [16 x 32] x [32 x 64]
-        uint32_t a1[2][4];
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int kt = 0; kt < 2; ++kt) {
-            const int r = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-            const int c = kt * 16 + (lane >> 4) * 8;
-            ldmatrix_x4(a1[kt], sbase + r * kNnRowBytes + c * 2);
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ReLU, then round to FP16 (negative values become +0 or -0, equal as a next-layer input).
+__device__ __forceinline__ uint32_t relu_pack_h2(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" :: "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// Byte offset of the 16-byte chunk j (elements 8j .. 8j + 7) of row m in a K-wide operand image.
+__device__ __forceinline__ uint32_t nn_chunk(int m, int j, int K) { return (m >> 3) * (K / 8) * 128 + j * 128 + (m & 7) * 16; }
+
+// ------------------------------------------------------------------------------ decode pipeline
+//
+// A block of 384 threads: 8 client warps (256 threads, one decode row each per round) and one
+// decode warpgroup (warps 8 .. 11). A round decodes 256 texels:
+//   1. each client thread writes its texel's 24 FP16 inputs (plus the two bias columns) as row
+//      `row` of the round's layer-1 operand and arrives on in_full[slot];
+//   2. the decode warpgroup runs the three layers as tcgen05 products of two M = 128 tiles (FP32
+//      accumulators and the FP16 hidden activations both in TMEM) and writes the
+//      8 FP32 outputs of each row over the consumed layer-1 operand, then arrives on
+//      out_full[slot];
+//   3. the client thread reads its row back (and, when sharing, its warp's other rows).
+// Two slots let the clients prepare round r + 1 while round r is decoded. Every wait is bounded:
+// one that gives up counts itself in flags[0], and all later waits of the launch return at once
+// (the outputs are then garbage, and the library reports the timeout).
+
+constexpr int kNnRows = 256;                       // texels per round
+constexpr int kNnPipeThreads = 384;
+constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: layer-1 operand, then 256 x 8 FP32 outputs
+// TMEM columns of a block: FP32 accumulators of the two tiles at 0 and 64 (64 columns each), and
+// the tiles' FP16 hidden activations (the A operand of layers 2 and 3, two K elements per
+// 32-bit column, K = 80 -> 40 columns) at 128 and 168.
+constexpr int kNnTmemCols = 256;
+constexpr int kNnHidCol = 128, kNnHidCols = kNnK2 / 2;
+constexpr unsigned kNnWaitLimit = 1u << 20;        // mbarrier polls before a wait gives up
+
+struct NnPipeSmem {
+    alignas(128) unsigned char b[kNnImgBytes];
+    alignas(128) unsigned char io[2][kNnIoBytes];
+    float4 rec[2][kNnRows];  // per-row sample records of the clients (see the render kernels)
+    unsigned long long in_full[2], out_full[2], mma[2];  // mma: one barrier per tile
+    uint32_t tmem;
+    int more[2];             // 1: the round in this slot carries rows, 0: the clients are done
+};
+
+// Bounded mbarrier waits of one thread.
+struct NnWaiter {
+    int* flags;
+    uint32_t dead;
+    __device__ __forceinline__ bool wait(const unsigned long long& bar, uint32_t parity)
+    {
+        if (dead) return false;
+        const uint32_t a = smem_u32(&bar);
+        for (unsigned it = 0;; ++it) {
+            if (nn_try_wait(a, parity)) return true;
+            if ((it & 1023u) == 1023u && *reinterpret_cast<volatile int*>(flags) != 0) break;
+            if (it >= kNnWaitLimit) {
+                atomicAdd(flags, 1);
+                break;
+            }
         }
-        float acc[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            nn_bias(acc[nt], nd.bias, nt, lane);
-#pragma unroll
-            for (int kt = 0; kt < 2; ++kt) mma_16816(acc[nt], a1[kt], __ldg(nd.wfrag + (kt * 8 + nt) * 32 + lane));
-        }
-        // layer 2: [16 x 64] x [64 x 64]
-        uint32_t a2[4][4];
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) nn_relu_pack(acc[2 * kt], acc[2 * kt + 1], a2[kt]);
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            nn_bias(acc[nt], nd.bias + kNnH, nt, lane);
-#pragma unroll
-            for (int kt = 0; kt < 4; ++kt) mma_16816(acc[nt], a2[kt], __ldg(nd.wfrag + (16 + kt * 8 + nt) * 32 + lane));
-        }
-        // layer 3: [16 x 64] x [64 x 8]
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) nn_relu_pack(acc[2 * kt], acc[2 * kt + 1], a2[kt]);
-        nn_bias(out[mt], nd.bias + 2 * kNnH, 0, lane);
-#pragma unroll
-        for (int kt = 0; kt < 4; ++kt) mma_16816(out[mt], a2[kt], __ldg(nd.wfrag + (48 + kt) * 32 + lane));
+        dead = 1;
+        return false;
     }
-    __syncwarp();  // every lane has read the A tile
-    // rows mt * 16 + lane / 4 (+ 8), columns 2 (lane % 4) + {0, 1} -> 48-byte rows
-    float* ob = reinterpret_cast<float*>(smem);
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-        const int r = mt * 16 + (lane >> 2);
-        const int c = 2 * (lane & 3);
-        *reinterpret_cast<float2*>(ob + r * 12 + c) = make_float2(out[mt][0], out[mt][1]);
-        *reinterpret_cast<float2*>(ob + (r + 8) * 12 + c) = make_float2(out[mt][2], out[mt][3]);
+};
+
+// Prologue (all 384 threads): weight images into shared memory, barriers, 128 TMEM columns
+// (allocated by warp 8, which also frees them).
+__device__ __forceinline__ void nn_pipe_setup(NnPipeSmem& sm, const NeuralDev* nd)
+{
+    const uint4* src = nd->wimg;
+    uint4* dst = reinterpret_cast<uint4*>(sm.b);
+    for (int i = threadIdx.x; i < kNnImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.in_full[0])), "r"(kNnRows) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.in_full[1])), "r"(kNnRows) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.out_full[0])), "r"(128) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.out_full[1])), "r"(128) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.mma[0])), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.mma[1])), "r"(1) : "memory");
     }
-    __syncwarp();
-    const float4 o0 = *reinterpret_cast<const float4*>(ob + lane * 12);
-    const float4 o1 = *reinterpret_cast<const float4*>(ob + lane * 12 + 4);
-    t[0] = o0.x; t[1] = o0.y; t[2] = o0.z; t[3] = o0.w;
-    t[4] = o1.x; t[5] = o1.y; t[6] = o1.z; t[7] = o1.w;
-    __syncwarp();  // the scratch may be rewritten by the next decode
+    if ((threadIdx.x >> 5) == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&sm.tmem)), "r"(kNnTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ __forceinline__ void nn_pipe_teardown(NnPipeSmem& sm)
+{
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 8)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(sm.tmem), "r"(kNnTmemCols) : "memory");
+}
+
+// ---- client side
+
+// Row `row` of the round's layer-1 operand: chunks 0..2 = the 24 inputs, chunk 3 = (1, 1, 0 ...)
+// (the columns that carry the bias, split into FP16 high and low parts, in the weight image).
+__device__ __forceinline__ void nn_put_inputs(NnPipeSmem& sm, int slot, int row, const uint32_t (&in)[12])
+{
+    const uint32_t base = smem_u32(sm.io[slot]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) sts128(base + nn_chunk(row, j, kNnK1), in[4 * j], in[4 * j + 1], in[4 * j + 2], in[4 * j + 3]);
+    sts128(base + nn_chunk(row, 3, kNnK1), 0x3c003c00u, 0u, 0u, 0u);
+}
+
+// Hands the slot's rows to the decoder (every client thread calls it once per round; thread 0
+// also says whether the round carries rows).
+__device__ __forceinline__ void nn_publish(NnPipeSmem& sm, int slot, int more)
+{
+    if (threadIdx.x == 0) sm.more[slot] = more;
+    fence_async_smem();
+    nn_arrive(smem_u32(&sm.in_full[slot]));
+}
+
+// The 8 decoded FP32 channels of row `row` (valid after out_full of its round).
+__device__ __forceinline__ void nn_get_outputs(const NnPipeSmem& sm, int slot, int row, float (&t)[8])
+{
+    const float4* o = reinterpret_cast<const float4*>(sm.io[slot] + row * 32);
+    const float4 a = o[0], b = o[1];
+    t[0] = a.x; t[1] = a.y; t[2] = a.z; t[3] = a.w;
+    t[4] = b.x; t[5] = b.y; t[6] = b.z; t[7] = b.w;
+}
+
+// ---- decode warpgroup
+
+// True on every thread of the decode warpgroup iff p holds on all of them (all 128 threads
+// execute it, so the loop below leaves on the same round everywhere).
+__device__ __forceinline__ bool nn_wg_all(bool p)
+{
+    uint32_t r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 2, 128, p;\n\t"
+                 "selp.u32 %0, 1, 0, q;\n}\n" : "=r"(r) : "r"((uint32_t)p) : "memory");
+    return r != 0;
+}
+
+
+// 64 consecutive FP32 columns of this thread's TMEM lane (two loads in flight, one wait).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
+{
+    uint32_t r[64];
+#define STF_LD32(OFF, R)                                                                                        \
+    asm volatile(                                                                                               \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"         \
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"                           \
+        : "=r"(R[0]), "=r"(R[1]), "=r"(R[2]), "=r"(R[3]), "=r"(R[4]), "=r"(R[5]), "=r"(R[6]), "=r"(R[7]),       \
+          "=r"(R[8]), "=r"(R[9]), "=r"(R[10]), "=r"(R[11]), "=r"(R[12]), "=r"(R[13]), "=r"(R[14]), "=r"(R[15]), \
+          "=r"(R[16]), "=r"(R[17]), "=r"(R[18]), "=r"(R[19]), "=r"(R[20]), "=r"(R[21]), "=r"(R[22]),            \
+          "=r"(R[23]), "=r"(R[24]), "=r"(R[25]), "=r"(R[26]), "=r"(R[27]), "=r"(R[28]), "=r"(R[29]),            \
+          "=r"(R[30]), "=r"(R[31])                                                                              \
+        : "r"(taddr + (OFF)))
+    STF_LD32(0, r);
+    STF_LD32(32, (r + 32));
+#undef STF_LD32
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive 32-bit columns of this thread's TMEM lane from registers.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n"
+        :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+           "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+           "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+           "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
+        :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+           "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Hidden-layer epilogue of one tile: this thread's TMEM lane (64 FP32 accumulator columns at
+// t_acc), ReLU, FP16, into the first 32 columns of the tile's hidden operand at t_hid.
+__device__ __forceinline__ void nn_hidden_epilogue(uint32_t t_acc, uint32_t t_hid)
+{
+    float v[64];
+    tmem_ld64(t_acc, v);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        uint32_t h[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[j] = relu_pack_h2(v[32 * q + 2 * j], v[32 * q + 2 * j + 1]);
+        tmem_st16(t_hid + 16 * q, h);
+    }
+    tmem_wait_st();
+}
+
+// Orders the warpgroup's TMEM writes before the products the leader issues next.
+__device__ __forceinline__ void nn_decode_sync()
+{
+    tc_fence_before();
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+    tc_fence_after();
+}
+
+// One layer's K / 16 products of one tile, issued by one thread and committed to the tile's
+// barrier. A from shared memory: a_desc / b_desc describe the first K step and a step advances
+// both by 256 bytes (16 in the descriptors' address field).
+template <int K>
+__device__ __forceinline__ void nn_issue_tile(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, uint32_t mbar)
+{
+#pragma unroll
+    for (int s = 0; s < K / 16; ++s) nn_mma(d_tmem, a_desc + 16 * s, b_desc + 16 * s, idesc, s > 0 ? 1u : 0u);
+    nn_commit(mbar);
+}
+
+// A from tensor memory: a K step advances A by 8 columns.
+template <int K>
+__device__ __forceinline__ void nn_issue_tile_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc, uint32_t mbar)
+{
+#pragma unroll
+    for (int s = 0; s < K / 16; ++s) nn_mma_ts(d_tmem, a_tmem + 8 * s, b_desc + 16 * s, idesc, s > 0 ? 1u : 0u);
+    nn_commit(mbar);
+}
+
+// The decode warpgroup's loop: one round per in_full phase until a round without rows. The two
+// M = 128 tiles of a round alternate: while the tensor cores run one tile's layer, the warpgroup
+// converts the other tile's previous layer, so each product's latency hides behind an epilogue.
+__device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
+{
+    const int m = threadIdx.x - kNnRows;  // 0 .. 127: row within a tile = TMEM lane
+    const bool leader = m == 0;
+    const uint32_t tmem = sm.tmem;
+    const uint32_t t_lane = tmem + ((uint32_t)(m & ~31) << 16);
+    const uint32_t b = smem_u32(sm.b);
+    const uint32_t bar[2] = {smem_u32(&sm.mma[0]), smem_u32(&sm.mma[1])};
+    // the constant bias columns of the hidden operands: K 64, 65 = 1, K 66 .. 79 = 0
+    {
+        const uint32_t c[8] = {0x3c003c00u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        tmem_st8(t_lane + kNnHidCol + 32, c);
+        tmem_st8(t_lane + kNnHidCol + kNnHidCols + 32, c);
+        tmem_wait_st();
+    }
+    constexpr uint32_t sbo1 = kNnK1 / 8 * 128, sbo2 = kNnK2 / 8 * 128;
+    const uint64_t b1 = nn_sdesc(b, 128, sbo1), b2 = nn_sdesc(b + kNnB1Bytes, 128, sbo2);
+    const uint64_t b3 = nn_sdesc(b + kNnB1Bytes + kNnB2Bytes, 128, sbo2);
+    NnWaiter w{flags, 0};
+    uint32_t ph[2] = {0u, 0u};
+    bool ok = true;
+    // waits for tile mt's pending products (every thread; leaves the loop together on a timeout)
+    auto tile_wait = [&](int mt) -> bool {
+        ok = nn_wg_all(w.wait(sm.mma[mt], ph[mt]));
+        ph[mt] ^= 1u;
+        tc_fence_after();
+        return ok;
+    };
+#pragma unroll 1
+    for (uint32_t r = 0;; ++r) {
+        const int slot = r & 1;
+        if (!nn_wg_all(w.wait(sm.in_full[slot], (r >> 1) & 1u))) break;
+        if (sm.more[slot] == 0) break;
+        tc_fence_after();
+        const uint32_t io = smem_u32(sm.io[slot]);
+        // layer 1 of both tiles: K = 32 (24 inputs, bias), N = 64
+        if (leader)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                nn_issue_tile<kNnK1>(tmem + mt * 64, nn_sdesc(io + mt * (kNnRows / 2 / 8) * sbo1, 128, sbo1), b1,
+                                     nn_idesc(64), bar[mt]);
+        // layers 2 and 3, tile by tile: epilogue of the previous layer, then the next products
+#pragma unroll
+        for (int layer = 2; layer <= 3 && ok; ++layer) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                if (!tile_wait(mt)) break;
+                nn_hidden_epilogue(t_lane + mt * 64, t_lane + kNnHidCol + mt * kNnHidCols);
+                nn_decode_sync();
+                if (leader) {
+                    const uint32_t a = tmem + kNnHidCol + mt * kNnHidCols;
+                    if (layer == 2) nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b2, nn_idesc(64), bar[mt]);
+                    else nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b3, nn_idesc(16), bar[mt]);
+                }
+            }
+        }
+        if (!ok) break;
+        // outputs: 8 FP32 per row over the consumed layer-1 operand
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            if (!tile_wait(mt)) break;
+            float o[8];
+            tmem_ld8(t_lane + mt * 64, o);
+            float4* dst = reinterpret_cast<float4*>(sm.io[slot] + (mt * 128 + m) * 32);
+            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
+        if (!ok) break;
+        // all TMEM reads of the round precede the next round's products
+        tc_fence_before();
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        nn_arrive(smem_u32(&sm.out_full[slot]));
+    }
+    // every thread leaves on the same round; a thread that gave up marks the rest of the launch
+    // (flags[0]), and the clients' bounded waits then return at once. Products may still be in
+    // flight after a timeout: wait for them (bounded) before TMEM is freed.
+    if (w.dead)
+        for (int mt = 0; mt < 2; ++mt)
+            for (unsigned it = 0; it < kNnWaitLimit && !nn_try_wait(bar[mt], ph[mt] ^ 1u); ++it) {}
 }
 
 }  // namespace stf

@@ -129,6 +129,15 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
         stf_status s = stf_validate_view(views[i], i, filter, reuse_mode);
         if (s != STF_OK) return s;
     }
+    // one persistent launch per material kind: neural views must share a decoder (its weights are
+    // staged once per block)
+    const void* decoder = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (views[i].tex->kind != K_NEURAL) continue;
+        if (decoder && views[i].tex->decoder != decoder)
+            return stf_fail(STF_ERR_INVALID_ARG, "stf_render_views_noalloc: view %d uses a second neural decoder", i);
+        decoder = views[i].tex->decoder;
+    }
     NoallocScratch* dev = nullptr;
     stf_status st = setup(&dev);
     if (st != STF_OK) return st;

@@ -219,17 +219,21 @@ stf_status ensure_buffers(size_t bytes, int counters)
 // per view and collected per variant.
 void build_groups(const stf_view* views, int n, int filter, int mode, std::vector<Group>& groups)
 {
-    std::map<int, int> gi;
+    // one group per material kind and, for neural textures, per decoder: a neural group's kernels
+    // stage one decoder's weights in shared memory
+    std::map<std::pair<int, const void*>, int> gi;
     std::vector<double> cost(n);
     for (int i = 0; i < n; ++i) {
         const int f = view_filter(views[i], filter);
         cost[i] = (double)views[i].width * views[i].height * (f == STF_FILTER_BSPLINE3 ? 1.5 : 1.0);
         const int k = views[i].tex->kind;
-        if (!gi.count(k) || (int)groups[gi[k]].views.size() == kBatchMaxViews) {
-            gi[k] = (int)groups.size();
+        const std::pair<int, const void*> key{k, k == K_NEURAL ? (const void*)views[i].tex->decoder : nullptr};
+        auto it = gi.find(key);
+        if (it == gi.end() || (int)groups[it->second].views.size() == kBatchMaxViews) {
+            gi[key] = (int)groups.size();
             groups.push_back(Group{k, {}, {}, 0});
         }
-        groups[gi[k]].views.push_back(i);
+        groups[gi[key]].views.push_back(i);
     }
     for (Group& g : groups) {
         std::stable_sort(g.views.begin(), g.views.end(), [&](int a, int b) { return cost[a] > cost[b]; });
