@@ -463,13 +463,12 @@ __device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
     const uint64_t b3 = nn_sdesc(b + kNnB1Bytes + kNnB2Bytes, 128, sbo2);
     NnWaiter w{flags, 0};
     uint32_t ph[2] = {0u, 0u};
-    bool ok = true;
-    // waits for tile mt's pending products (every thread; leaves the loop together on a timeout)
-    auto tile_wait = [&](int mt) -> bool {
-        ok = nn_wg_all(w.wait(sm.mma[mt], ph[mt]));
+    // waits for tile mt's pending products; a thread whose wait gives up carries on with garbage
+    // (it passes the same barriers as the others) and the round-start vote ends the loop
+    auto tile_wait = [&](int mt) {
+        w.wait(sm.mma[mt], ph[mt]);
         ph[mt] ^= 1u;
         tc_fence_after();
-        return ok;
     };
 #pragma unroll 1
     for (uint32_t r = 0;; ++r) {
@@ -486,10 +485,10 @@ __device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
                                      nn_idesc(64), bar[mt]);
         // layers 2 and 3, tile by tile: epilogue of the previous layer, then the next products
 #pragma unroll
-        for (int layer = 2; layer <= 3 && ok; ++layer) {
+        for (int layer = 2; layer <= 3; ++layer) {
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-                if (!tile_wait(mt)) break;
+                tile_wait(mt);
                 nn_hidden_epilogue(t_lane + mt * 64, t_lane + kNnHidCol + mt * kNnHidCols);
                 nn_decode_sync();
                 if (leader) {
@@ -499,18 +498,16 @@ __device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
                 }
             }
         }
-        if (!ok) break;
         // outputs: 8 FP32 per row over the consumed layer-1 operand
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
-            if (!tile_wait(mt)) break;
+            tile_wait(mt);
             float o[8];
             tmem_ld8(t_lane + mt * 64, o);
             float4* dst = reinterpret_cast<float4*>(sm.io[slot] + (mt * 128 + m) * 32);
             dst[0] = make_float4(o[0], o[1], o[2], o[3]);
             dst[1] = make_float4(o[4], o[5], o[6], o[7]);
         }
-        if (!ok) break;
         // all TMEM reads of the round precede the next round's products
         tc_fence_before();
         asm volatile("bar.sync 2, 128;" ::: "memory");
