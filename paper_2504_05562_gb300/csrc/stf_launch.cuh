@@ -48,7 +48,7 @@ static cudaError_t launch_one(const DevView& v, cudaStream_t s)
         constexpr int dyn = (int)sizeof(NnPipeSmem);
         cudaError_t e = prepare_dynamic(k_render_neural<F, MODE, TW, TH>, dyn, kNnPipeThreads, cached, &per_sm);
         if (e != cudaSuccess) return e;
-        const long long groups = (long long)grid.x * grid.y;
+        const long long groups = (long long)((v.tiles_x + kNnClientWarps - 1) / kNnClientWarps) * v.tiles_y;
         const unsigned blocks = (unsigned)(groups < (long long)per_sm * device_sms() ? groups : (long long)per_sm * device_sms());
         k_render_neural<F, MODE, TW, TH><<<blocks, kNnPipeThreads, dyn, s>>>(v);
     } else {
@@ -129,7 +129,7 @@ struct NnConstViews {
     __device__ __forceinline__ const DevView& operator()(int i) const { return c_batch_views[i]; }
 };
 
-// The neural kind's multi-view kernel: the same work items, rendered by the 8 client warps of the
+// The neural kind's multi-view kernel: the same work items, rendered by the client warps of the
 // decode pipeline (all of a batch's neural views share one decoder; view 0 names it). The client
 // warps pull items together (named barrier 1), so every client takes the same rounds.
 template <int MODE, int F, int TW, int TH>
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2)
     __shared__ WorkItem sw;
     NnPipeSmem& sm = *reinterpret_cast<NnPipeSmem*>(dyn);
     nn_pipe_setup(sm, reinterpret_cast<const NeuralDev*>(c_batch_views[0].neural));
-    if (threadIdx.x >= kNnRows) {
+    if (threadIdx.x >= kNnClients) {
         nn_decode_role(sm, c_batch_views[0].flags);
     } else {
         const int warp = threadIdx.x >> 5;
@@ -152,15 +152,15 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2)
                 const int it = atomicAdd(counter, 1);
                 sw = it < n_items ? items[it] : WorkItem{-1, 0, 0, 0};
             }
-            asm volatile("bar.sync 1, 256;" ::: "memory");
+            asm volatile("bar.sync 1, %0;" :: "n"(kNnClients) : "memory");
             const WorkItem w = sw;
-            asm volatile("bar.sync 1, 256;" ::: "memory");  // sw is rewritten by the next pull
+            asm volatile("bar.sync 1, %0;" :: "n"(kNnClients) : "memory");  // sw is rewritten by the next pull
             if (w.view < 0) break;
             const DevView& v = c_batch_views[w.view];
-            const int groups = (w.ntiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+            const int groups = (w.ntiles + kNnClientWarps - 1) / kNnClientWarps;
 #pragma unroll 1
             for (int k = 0; k < groups; ++k) {
-                const int j = k * kWarpsPerBlock + warp;
+                const int j = k * kNnClientWarps + warp;
                 const bool active = j < w.ntiles;
                 const int t = w.tile0 + (active ? j : 0);
                 const int ty = t / v.tiles_x;

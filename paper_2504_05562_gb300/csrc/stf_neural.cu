@@ -317,14 +317,14 @@ __global__ void k_nn_export(const float* P, const float* lat, long long nlat, __
 }
 
 // Decodes a list of texels (packed ix | iy << 16) through the decode pipeline: persistent blocks,
-// 256 texels per round (a tail round decodes fewer rows).
+// kNnClients texels per round (a tail round decodes fewer rows).
 __global__ void __launch_bounds__(kNnPipeThreads, 2) k_nn_decode_list(const NeuralDev* nd, const int* idx, int n, int W,
                                                                       int H, float* out, int* flags)
 {
     extern __shared__ __align__(128) unsigned char dyn[];
     NnPipeSmem& sm = *reinterpret_cast<NnPipeSmem*>(dyn);
     nn_pipe_setup(sm, nd);
-    if (threadIdx.x >= kNnRows) {
+    if (threadIdx.x >= kNnClients) {
         nn_decode_role(sm, flags);
     } else {
         const int row = threadIdx.x;
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2) k_nn_decode_list(const Neur
         uint32_t r = 0;
         int prev = -1;
 #pragma unroll 1
-        for (int base = blockIdx.x * kNnRows;; base += gridDim.x * kNnRows) {
+        for (int base = blockIdx.x * kNnClients;; base += gridDim.x * kNnClients) {
             const bool more = base < n;
             const int i = base + row;
             if (more && i < n) {
@@ -668,7 +668,7 @@ extern "C" stf_status stf_decoder_decode(const stf_decoder* d, const int32_t* te
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int rounds = (n + kNnRows - 1) / kNnRows;
+    const int rounds = (n + kNnClients - 1) / kNnClients;
     const int blocks = rounds < per_sm * sms ? rounds : per_sm * sms;
     k_nn_decode_list<<<blocks, kNnPipeThreads, sizeof(NnPipeSmem), stf_stream()>>>(d->dev, texels, n, d->cfg.tex_w, d->cfg.tex_h, out, flags);
     e = cudaGetLastError();

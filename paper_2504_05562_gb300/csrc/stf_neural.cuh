@@ -68,44 +68,70 @@ __device__ __forceinline__ void nn_axis(int i, const NeuralDev& nd, int G, int& 
     c1 = clampi(a + 1, 0, G - 1);
 }
 
-// The 24 FP16 inputs of texel (x, y) as 12 packed words (interpolation rounded per operation in
-// the order (w00 L00 + w10 L10) + w01 L01, + w11 L11).
-__device__ __forceinline__ void nn_inputs(const NeuralDev& nd, int x, int y, uint32_t (&row)[12])
+// The four latent cells texel (x, y) interpolates (c[0..3] = (x0, y0), (x1, y0), (x0, y1),
+// (x1, y1), 2 x 16 bytes each) and their bilinear weights.
+__device__ __forceinline__ void nn_cells(const NeuralDev& nd, int x, int y, const uint4* (&c)[4], float (&w)[4])
 {
     int x0, x1, y0, y1;
     float fx, fy;
     nn_axis(x, nd, nd.gw, x0, x1, fx);
     nn_axis(y, nd, nd.gh, y0, y1, fy);
     const float gx = __fsub_rn(1.0f, fx), gy = __fsub_rn(1.0f, fy);
-    const float w00 = __fmul_rn(gx, gy), w10 = __fmul_rn(fx, gy), w01 = __fmul_rn(gx, fy), w11 = __fmul_rn(fx, fy);
-    const uint4* c00 = nd.lat16 + 2 * ((size_t)y0 * nd.gw + x0);
-    const uint4* c10 = nd.lat16 + 2 * ((size_t)y0 * nd.gw + x1);
-    const uint4* c01 = nd.lat16 + 2 * ((size_t)y1 * nd.gw + x0);
-    const uint4* c11 = nd.lat16 + 2 * ((size_t)y1 * nd.gw + x1);
+    w[0] = __fmul_rn(gx, gy);
+    w[1] = __fmul_rn(fx, gy);
+    w[2] = __fmul_rn(gx, fy);
+    w[3] = __fmul_rn(fx, fy);
+    c[0] = nd.lat16 + 2 * ((size_t)y0 * nd.gw + x0);
+    c[1] = nd.lat16 + 2 * ((size_t)y0 * nd.gw + x1);
+    c[2] = nd.lat16 + 2 * ((size_t)y1 * nd.gw + x0);
+    c[3] = nd.lat16 + 2 * ((size_t)y1 * nd.gw + x1);
+}
+
+// The 16 interpolated latents as 8 packed FP16 words from the cells' 8 chunks L[2 q + h] (cell q,
+// half h), rounded per operation in the order (w00 L00 + w10 L10) + w01 L01, + w11 L11 (pairs
+// of channels per f32x2 operation, each lane rounded as a scalar operation would be).
+__device__ __forceinline__ void nn_interp(const uint4 (&L)[8], const float (&w)[4], uint32_t (&row)[12])
+{
+    const float2 w0 = make_float2(w[0], w[0]), w1 = make_float2(w[1], w[1]);
+    const float2 w2 = make_float2(w[2], w[2]), w3 = make_float2(w[3], w[3]);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const uint4 a = __ldg(c00 + h), b = __ldg(c10 + h), c = __ldg(c01 + h), d = __ldg(c11 + h);
+        const uint4 a = L[h], b = L[2 + h], c = L[4 + h], d = L[6 + h];
         const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
         const uint32_t cw[4] = {c.x, c.y, c.z, c.w}, dw[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float2 A = unpack_h2(aw[k]), B = unpack_h2(bw[k]), Cc = unpack_h2(cw[k]), D = unpack_h2(dw[k]);
-            float s0 = __fmul_rn(w00, A.x), s1 = __fmul_rn(w00, A.y);
-            s0 = __fadd_rn(s0, __fmul_rn(w10, B.x));
-            s1 = __fadd_rn(s1, __fmul_rn(w10, B.y));
-            s0 = __fadd_rn(s0, __fmul_rn(w01, Cc.x));
-            s1 = __fadd_rn(s1, __fmul_rn(w01, Cc.y));
-            s0 = __fadd_rn(s0, __fmul_rn(w11, D.x));
-            s1 = __fadd_rn(s1, __fmul_rn(w11, D.y));
-            row[4 * h + k] = pack_h2(s0, s1);
+            float2 s2 = __fmul2_rn(w0, unpack_h2(aw[k]));
+            s2 = __fadd2_rn(s2, __fmul2_rn(w1, unpack_h2(bw[k])));
+            s2 = __fadd2_rn(s2, __fmul2_rn(w2, unpack_h2(cw[k])));
+            s2 = __fadd2_rn(s2, __fmul2_rn(w3, unpack_h2(dw[k])));
+            row[4 * h + k] = pack_h2(s2.x, s2.y);
         }
     }
+}
+
+// The position features of texel (x, y) as packed FP16 words 8 .. 11.
+__device__ __forceinline__ void nn_features(const NeuralDev& nd, int x, int y, uint32_t (&row)[12])
+{
     const int mask = (1 << nd.rshift) - 1;
     const uint2 fxw = nd.feat[x & mask], fyw = nd.feat[y & mask];
     row[8] = fxw.x;
     row[9] = fxw.y;
     row[10] = fyw.x;
     row[11] = fyw.y;
+}
+
+// The 24 FP16 inputs of texel (x, y) as 12 packed words.
+__device__ __forceinline__ void nn_inputs(const NeuralDev& nd, int x, int y, uint32_t (&row)[12])
+{
+    const uint4* c[4];
+    float w[4];
+    nn_cells(nd, x, y, c, w);
+    uint4 L[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { L[2 * q] = __ldg(c[q]); L[2 * q + 1] = __ldg(c[q] + 1); }
+    nn_interp(L, w, row);
+    nn_features(nd, x, y, row);
 }
 
 // ------------------------------------------------------------------------------ tcgen05 primitives
@@ -211,21 +237,27 @@ __device__ __forceinline__ uint32_t nn_chunk(int m, int j, int K) { return (m >>
 
 // ------------------------------------------------------------------------------ decode pipeline
 //
-// A block of 384 threads: 8 client warps (256 threads, one decode row each per round) and one
-// decode warpgroup (warps 8 .. 11). A round decodes 256 texels:
+// A block of 416 threads: 8 client warps (one decode row per thread and round), one MMA warp
+// (warp 8) and four epilogue warps (9 .. 12; warp w reaches TMEM lanes 32 (w mod 4) .. + 31, so
+// together they cover all 128). A round decodes the clients' 256 texels as two M = 128 tiles:
 //   1. each client thread writes its texel's 24 FP16 inputs (plus the two bias columns) as row
 //      `row` of the round's layer-1 operand and arrives on in_full[slot];
-//   2. the decode warpgroup runs the three layers as tcgen05 products of two M = 128 tiles (FP32
-//      accumulators and the FP16 hidden activations both in TMEM) and writes the
-//      8 FP32 outputs of each row over the consumed layer-1 operand, then arrives on
-//      out_full[slot];
-//   3. the client thread reads its row back (and, when sharing, its warp's other rows).
+//   2. the MMA warp issues the three layers' tcgen05 products of both tiles (FP32 accumulators in
+//      TMEM); between layers the epilogue warpgroup turns a tile's accumulators into FP16
+//      activations (ReLU) in TMEM, the A operand of the next layer, and arrives on epi[tile]; the
+//      tiles alternate, so one tile's products overlap the other's epilogue;
+//   3. the epilogue warpgroup writes the 8 FP32 outputs of each row over the consumed layer-1
+//      operand and arrives on out_full[slot]; the client threads read their rows back (and, when
+//      sharing, their warp's other rows).
 // Two slots let the clients prepare round r + 1 while round r is decoded. Every wait is bounded:
 // one that gives up counts itself in flags[0], and all later waits of the launch return at once
 // (the outputs are then garbage, and the library reports the timeout).
 
-constexpr int kNnRows = 256;                       // texels per round
-constexpr int kNnPipeThreads = 384;
+constexpr int kNnClientWarps = 8;
+constexpr int kNnClients = kNnClientWarps * 32;    // 256 texels per round
+constexpr int kNnMmaWarp = 8;
+constexpr int kNnRows = 256;                       // operand rows per round (two M = 128 tiles)
+constexpr int kNnPipeThreads = 416;
 constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: layer-1 operand, then 256 x 8 FP32 outputs
 // TMEM columns of a block: FP32 accumulators of the two tiles at 0 and 64 (64 columns each), and
 // the tiles' FP16 hidden activations (the A operand of layers 2 and 3, two K elements per
@@ -233,12 +265,15 @@ constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: layer-1 operand, th
 constexpr int kNnTmemCols = 256;
 constexpr int kNnHidCol = 128, kNnHidCols = kNnK2 / 2;
 constexpr unsigned kNnWaitLimit = 1u << 20;        // mbarrier polls before a wait gives up
+constexpr int kNnStageBytes = 144;                 // 8 x 16-byte latent chunks + a 16-byte record
 
 struct NnPipeSmem {
     alignas(128) unsigned char b[kNnImgBytes];
     alignas(128) unsigned char io[2][kNnIoBytes];
     float4 rec[2][kNnRows];  // per-row sample records of the clients (see the render kernels)
-    unsigned long long in_full[2], out_full[2], mma[2];  // mma: one barrier per tile
+    // per client: the 8 latent chunks of its next texel, copied ahead (cp.async), and its record
+    alignas(16) unsigned char stage[kNnClients][kNnStageBytes];
+    unsigned long long in_full[2], out_full[2], mma[2], epi[2];  // mma, epi: one barrier per tile
     uint32_t tmem;
     int more[2];             // 1: the round in this slot carries rows, 0: the clients are done
 };
@@ -264,7 +299,7 @@ struct NnWaiter {
     }
 };
 
-// Prologue (all 384 threads): weight images into shared memory, barriers, 128 TMEM columns
+// Prologue (all threads): weight images into shared memory, barriers, the TMEM columns
 // (allocated by warp 8, which also frees them).
 __device__ __forceinline__ void nn_pipe_setup(NnPipeSmem& sm, const NeuralDev* nd)
 {
@@ -272,8 +307,10 @@ __device__ __forceinline__ void nn_pipe_setup(NnPipeSmem& sm, const NeuralDev* n
     uint4* dst = reinterpret_cast<uint4*>(sm.b);
     for (int i = threadIdx.x; i < kNnImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.in_full[0])), "r"(kNnRows) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.in_full[1])), "r"(kNnRows) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.in_full[0])), "r"(kNnClients) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.in_full[1])), "r"(kNnClients) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.epi[0])), "r"(128) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.epi[1])), "r"(128) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.out_full[0])), "r"(128) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.out_full[1])), "r"(128) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.mma[0])), "r"(1) : "memory");
@@ -321,6 +358,39 @@ __device__ __forceinline__ void nn_publish(NnPipeSmem& sm, int slot, int more)
     nn_arrive(smem_u32(&sm.in_full[slot]));
 }
 
+// Starts copying the 8 latent chunks of texel (x, y) into this client's stage (asynchronous;
+// nn_stage_inputs waits for them).
+__device__ __forceinline__ void nn_stage_issue(NnPipeSmem& sm, int client, const NeuralDev& nd, int x, int y)
+{
+    const uint4* c[4];
+    float w[4];
+    nn_cells(nd, x, y, c, w);
+    const uint32_t dst = smem_u32(sm.stage[client]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(dst + (2 * q + h) * 16),
+                         "l"(__cvta_generic_to_global(c[q] + h)) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The 24 FP16 inputs of texel (x, y) from the chunks staged by nn_stage_issue.
+__device__ __forceinline__ void nn_stage_inputs(const NnPipeSmem& sm, int client, const NeuralDev& nd, int x, int y,
+                                                uint32_t (&row)[12])
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    const uint4* c[4];
+    float w[4];
+    nn_cells(nd, x, y, c, w);
+    const uint4* st = reinterpret_cast<const uint4*>(sm.stage[client]);
+    uint4 L[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) L[i] = st[i];
+    nn_interp(L, w, row);
+    nn_features(nd, x, y, row);
+}
+
 // The 8 decoded FP32 channels of row `row` (valid after out_full of its round).
 __device__ __forceinline__ void nn_get_outputs(const NnPipeSmem& sm, int slot, int row, float (&t)[8])
 {
@@ -331,17 +401,6 @@ __device__ __forceinline__ void nn_get_outputs(const NnPipeSmem& sm, int slot, i
 }
 
 // ---- decode warpgroup
-
-// True on every thread of the decode warpgroup iff p holds on all of them (all 128 threads
-// execute it, so the loop below leaves on the same round everywhere).
-__device__ __forceinline__ bool nn_wg_all(bool p)
-{
-    uint32_t r;
-    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 2, 128, p;\n\t"
-                 "selp.u32 %0, 1, 0, q;\n}\n" : "=r"(r) : "r"((uint32_t)p) : "memory");
-    return r != 0;
-}
-
 
 // 64 consecutive FP32 columns of this thread's TMEM lane (two loads in flight, one wait).
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64])
@@ -412,14 +471,6 @@ __device__ __forceinline__ void nn_hidden_epilogue(uint32_t t_acc, uint32_t t_hi
     tmem_wait_st();
 }
 
-// Orders the warpgroup's TMEM writes before the products the leader issues next.
-__device__ __forceinline__ void nn_decode_sync()
-{
-    tc_fence_before();
-    asm volatile("bar.sync 2, 128;" ::: "memory");
-    tc_fence_after();
-}
-
 // One layer's K / 16 products of one tile, issued by one thread and committed to the tile's
 // barrier. A from shared memory: a_desc / b_desc describe the first K step and a step advances
 // both by 256 bytes (16 in the descriptors' address field).
@@ -440,17 +491,63 @@ __device__ __forceinline__ void nn_issue_tile_ts(uint32_t d_tmem, uint32_t a_tme
     nn_commit(mbar);
 }
 
-// The decode warpgroup's loop: one round per in_full phase until a round without rows. The two
-// M = 128 tiles of a round alternate: while the tensor cores run one tile's layer, the warpgroup
-// converts the other tile's previous layer, so each product's latency hides behind an epilogue.
-__device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
+// The MMA warp (lane 0 issues): per round, wait for the clients' rows and for the previous round's
+// outputs to have left TMEM, issue layer 1 of both tiles, then each later layer of a tile as soon
+// as the epilogue warpgroup has stored that tile's activations.
+__device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
 {
-    const int m = threadIdx.x - kNnRows;  // 0 .. 127: row within a tile = TMEM lane
-    const bool leader = m == 0;
-    const uint32_t tmem = sm.tmem;
-    const uint32_t t_lane = tmem + ((uint32_t)(m & ~31) << 16);
-    const uint32_t b = smem_u32(sm.b);
+    const uint32_t tmem = sm.tmem, b = smem_u32(sm.b);
     const uint32_t bar[2] = {smem_u32(&sm.mma[0]), smem_u32(&sm.mma[1])};
+    constexpr uint32_t sbo1 = kNnK1 / 8 * 128, sbo2 = kNnK2 / 8 * 128;
+    const uint64_t b1 = nn_sdesc(b, 128, sbo1), b2 = nn_sdesc(b + kNnB1Bytes, 128, sbo2);
+    const uint64_t b3 = nn_sdesc(b + kNnB1Bytes + kNnB2Bytes, 128, sbo2);
+    const bool leader = (threadIdx.x & 31) == 0;
+    NnWaiter w{flags, 0};
+    uint32_t eph[2] = {0u, 0u}, commits = 0;  // products committed per tile
+#pragma unroll 1
+    for (uint32_t r = 0;; ++r) {
+        const int slot = r & 1;
+        w.wait(sm.in_full[slot], (r >> 1) & 1u);
+        if (__shfl_sync(0xffffffffu, sm.more[slot], 0) == 0 || __any_sync(0xffffffffu, w.dead)) break;
+        if (r > 0) w.wait(sm.out_full[(r - 1) & 1], ((r - 1) >> 1) & 1u);  // TMEM reads of round r - 1 done
+        tc_fence_after();
+        const uint32_t io = smem_u32(sm.io[slot]);
+        if (leader)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                nn_issue_tile<kNnK1>(tmem + mt * 64, nn_sdesc(io + mt * (kNnRows / 2 / 8) * sbo1, 128, sbo1), b1,
+                                     nn_idesc(64), bar[mt]);
+        commits += 3;
+#pragma unroll
+        for (int layer = 2; layer <= 3; ++layer) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                w.wait(sm.epi[mt], eph[mt]);
+                eph[mt] ^= 1u;
+                tc_fence_after();
+                if (leader) {
+                    const uint32_t a = tmem + kNnHidCol + mt * kNnHidCols;
+                    if (layer == 2) nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b2, nn_idesc(64), bar[mt]);
+                    else nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b3, nn_idesc(16), bar[mt]);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    // after a timeout, products may still be in flight: wait (bounded) for each tile's last commit
+    // before the teardown frees TMEM
+    if (leader && commits > 0 && w.dead)
+        for (int mt = 0; mt < 2; ++mt)
+            for (unsigned it = 0; it < kNnWaitLimit && !nn_try_wait(bar[mt], (commits - 1) & 1u); ++it) {}
+}
+
+// The epilogue warpgroup: per round and tile, turn layer 1 and 2 accumulators into the next
+// layer's FP16 activations (in TMEM), then write the layer-3 outputs to shared memory.
+__device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
+{
+    // row within a tile = TMEM lane: a warp reaches the 32 lanes of quarter (warp id mod 4)
+    const int m = (((int)threadIdx.x >> 5) & 3) * 32 + ((int)threadIdx.x & 31);
+    const uint32_t t_lane = sm.tmem + ((uint32_t)(m & ~31) << 16);
     // the constant bias columns of the hidden operands: K 64, 65 = 1, K 66 .. 79 = 0
     {
         const uint32_t c[8] = {0x3c003c00u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
@@ -458,13 +555,8 @@ __device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
         tmem_st8(t_lane + kNnHidCol + kNnHidCols + 32, c);
         tmem_wait_st();
     }
-    constexpr uint32_t sbo1 = kNnK1 / 8 * 128, sbo2 = kNnK2 / 8 * 128;
-    const uint64_t b1 = nn_sdesc(b, 128, sbo1), b2 = nn_sdesc(b + kNnB1Bytes, 128, sbo2);
-    const uint64_t b3 = nn_sdesc(b + kNnB1Bytes + kNnB2Bytes, 128, sbo2);
     NnWaiter w{flags, 0};
     uint32_t ph[2] = {0u, 0u};
-    // waits for tile mt's pending products; a thread whose wait gives up carries on with garbage
-    // (it passes the same barriers as the others) and the round-start vote ends the loop
     auto tile_wait = [&](int mt) {
         w.wait(sm.mma[mt], ph[mt]);
         ph[mt] ^= 1u;
@@ -473,32 +565,19 @@ __device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
 #pragma unroll 1
     for (uint32_t r = 0;; ++r) {
         const int slot = r & 1;
-        if (!nn_wg_all(w.wait(sm.in_full[slot], (r >> 1) & 1u))) break;
-        if (sm.more[slot] == 0) break;
-        tc_fence_after();
-        const uint32_t io = smem_u32(sm.io[slot]);
-        // layer 1 of both tiles: K = 32 (24 inputs, bias), N = 64
-        if (leader)
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-                nn_issue_tile<kNnK1>(tmem + mt * 64, nn_sdesc(io + mt * (kNnRows / 2 / 8) * sbo1, 128, sbo1), b1,
-                                     nn_idesc(64), bar[mt]);
-        // layers 2 and 3, tile by tile: epilogue of the previous layer, then the next products
+        w.wait(sm.in_full[slot], (r >> 1) & 1u);
+        // leave together per warp (the TMEM accesses below are warp-collective)
+        if (__shfl_sync(0xffffffffu, sm.more[slot], 0) == 0 || __any_sync(0xffffffffu, w.dead)) break;
 #pragma unroll
         for (int layer = 2; layer <= 3; ++layer) {
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
                 tile_wait(mt);
                 nn_hidden_epilogue(t_lane + mt * 64, t_lane + kNnHidCol + mt * kNnHidCols);
-                nn_decode_sync();
-                if (leader) {
-                    const uint32_t a = tmem + kNnHidCol + mt * kNnHidCols;
-                    if (layer == 2) nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b2, nn_idesc(64), bar[mt]);
-                    else nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b3, nn_idesc(16), bar[mt]);
-                }
+                tc_fence_before();
+                nn_arrive(smem_u32(&sm.epi[mt]));
             }
         }
-        // outputs: 8 FP32 per row over the consumed layer-1 operand
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
             tile_wait(mt);
@@ -508,17 +587,16 @@ __device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
             dst[0] = make_float4(o[0], o[1], o[2], o[3]);
             dst[1] = make_float4(o[4], o[5], o[6], o[7]);
         }
-        // all TMEM reads of the round precede the next round's products
         tc_fence_before();
-        asm volatile("bar.sync 2, 128;" ::: "memory");
         nn_arrive(smem_u32(&sm.out_full[slot]));
     }
-    // every thread leaves on the same round; a thread that gave up marks the rest of the launch
-    // (flags[0]), and the clients' bounded waits then return at once. Products may still be in
-    // flight after a timeout: wait for them (bounded) before TMEM is freed.
-    if (w.dead)
-        for (int mt = 0; mt < 2; ++mt)
-            for (unsigned it = 0; it < kNnWaitLimit && !nn_try_wait(bar[mt], ph[mt] ^ 1u); ++it) {}
+}
+
+// The decode side of a pipeline block (threads kNnClients .. kNnPipeThreads - 1).
+__device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
+{
+    if ((threadIdx.x >> 5) == kNnMmaWarp) nn_mma_role(sm, flags);
+    else nn_epilogue_role(sm, flags);
 }
 
 }  // namespace stf

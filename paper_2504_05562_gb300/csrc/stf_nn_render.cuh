@@ -1,9 +1,9 @@
 // Rendering a neural material: the per-pixel steps of the texture kinds (pixel -> uv, random
 // numbers, one-tap texel choice, sharing with the bounded weighted-importance combine, shading)
-// run on the 8 client warps of the decode pipeline, split around the decode:
+// run on the client warps of the decode pipeline, split around the decode:
 //   produce: the pixel's chosen texel (or, for the full filter, one tap per round) -> its sample
 //            record and its 24 decoder inputs as a row of the round;
-//   consume: after the decode warpgroup has finished the round, the decoded texels of the warp's
+//   consume: after the decoder has finished the round, the decoded texels of the warp's
 //            rows -> the estimate of Eq. estimator-for-stf (or the running filter sum) -> shaded
 //            output.
 // Round r is produced before round r - 1 is consumed, so the clients' arithmetic overlaps the
@@ -20,7 +20,7 @@
 namespace stf {
 
 // Per-warp B-spline tap-weight table of the sharing loop: 8 columns of 32 lanes.
-constexpr int kNnWtabFloats = kWarpsPerBlock * 32 * 8;
+constexpr int kNnWtabFloats = kNnClientWarps * 32 * 8;
 
 // The client side of one block. VIEWS maps a view index to its constants (a kernel parameter or
 // the batch's constant bank). Every client thread calls round() for the same rounds.
@@ -215,7 +215,7 @@ struct NnParamView {
     __device__ __forceinline__ const DevView& operator()(int) const { return *v; }
 };
 
-// One view: persistent blocks walk the 8-tile groups (8 tiles of one tile row) of the view.
+// One view: persistent blocks walk the view's tile groups (kNnClientWarps tiles of one tile row).
 template <int F, int MODE, int TW, int TH>
 __global__ void __launch_bounds__(kNnPipeThreads, 2) k_render_neural(const __grid_constant__ DevView v)
 {
@@ -223,17 +223,17 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2) k_render_neural(const __gri
     __shared__ float wtabs[kNnWtabFloats];
     NnPipeSmem& sm = *reinterpret_cast<NnPipeSmem*>(dyn);
     nn_pipe_setup(sm, reinterpret_cast<const NeuralDev*>(v.neural));
-    if (threadIdx.x >= kNnRows) {
+    if (threadIdx.x >= kNnClients) {
         nn_decode_role(sm, v.flags);
     } else {
         const int warp = threadIdx.x >> 5;
         NnRenderClient<F, MODE, TW, TH, NnParamView> cl(sm, wtabs + warp * 256, NnParamView{&v}, v.flags);
-        const int gx = (v.tiles_x + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        const int gx = (v.tiles_x + kNnClientWarps - 1) / kNnClientWarps;
         const int groups = gx * v.tiles_y;
 #pragma unroll 1
         for (int g = blockIdx.x; g < groups; g += gridDim.x) {
             const int by = g / gx;
-            const int tx = (g - by * gx) * kWarpsPerBlock + warp;
+            const int tx = (g - by * gx) * kNnClientWarps + warp;
             cl.group(0, tx < v.tiles_x, tx, by);
         }
         cl.finish();
