@@ -25,6 +25,7 @@ LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 BILINEAR, BSPLINE3 = 0, 1
 FULL, ONE_TAP, QUAD2, WAVE2, WAVE3, WAVE4 = 0, 1, 2, 3, 4, 5
+FLAG_EXACT = 16  # exact filtering (bilinear), OR'd into a sharing mode
 FP32, FP16, BF16, E4M3, UNORM8 = 0, 1, 2, 3, 4
 
 _lock = threading.Lock()

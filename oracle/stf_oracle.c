@@ -445,7 +445,8 @@ int stf_ref_shade_sensitivity(const ref_view* v, int C, const float* ch, double*
 typedef struct {
     const ref_material* m;
     const ref_view* v;
-    int mode;
+    int mode;                /* sharing mode without flags */
+    int exact;               /* REF_FLAG_EXACT given */
     uint64_t seed;
     float* out_rgba;
     uint32_t* out_idx;
@@ -459,6 +460,38 @@ static void final_rgba(const ref_view* v, int C, const float* f, float u, float 
 {
     if (v->shading) { stf_ref_shade(v, f, u, w, rgba); return; }
     for (int k = 0; k < 4; ++k) rgba[k] = k < C ? f[k] : (k == 3 ? 1.0f : 0.0f);
+}
+
+/* The deterministic filter at (cx, cy): sum over the lattice taps of W(dx) W(dy) T, y outer,
+ * x inner, into res. With samples (n > 0: lattice indices six/siy of the lanes in list), every
+ * tap of positive weight must be one of the samples and takes that sample's texel; if one is
+ * missing, res is left unchanged and 0 is returned. */
+static int full_filter(const ref_material* m, int f, int C, float cx, float cy, const int* six, const int* siy,
+                       const int* list, int n, float* res)
+{
+    int i0x = (int)floorf(cx), i0y = (int)floorf(cy);
+    int k0 = tap_first(f), nt = tap_count(f);
+    float acc[REF_MAX_CH] = {0};
+    float Tt[REF_MAX_CH];
+    for (int s = 0; s < nt; ++s) {
+        int ny = i0y + k0 + s;
+        float wy = stf_ref_weight(f, cy - (float)ny);
+        for (int t = 0; t < nt; ++t) {
+            int nx = i0x + k0 + t;
+            float wx = stf_ref_weight(f, cx - (float)nx);
+            float w = wx * wy;
+            if (n > 0 && w > 0.0f) {
+                int found = 0;
+                for (int i = 0; i < n && !found; ++i) found = six[list[i]] == nx && siy[list[i]] == ny;
+                if (!found) return 0;
+            }
+            /* a sampled texel is the fetch at its lattice index, so fetching here is the same */
+            fetch_texel(m, nx, ny, Tt);
+            for (int c = 0; c < C; ++c) acc[c] = acc[c] + w * Tt[c];
+        }
+    }
+    for (int c = 0; c < C; ++c) res[c] = acc[c];
+    return 1;
 }
 
 static void render_tile(const job_t* J, int tx, int ty)
@@ -491,20 +524,7 @@ static void render_tile(const job_t* J, int tx, int ty)
         float res[REF_MAX_CH] = {0};
         if (J->mode == REF_FULL) {
             /* deterministic filter: sum over the lattice taps of W(dx) W(dy) T, y outer */
-            int i0x = (int)floorf(cx[lane]), i0y = (int)floorf(cy[lane]);
-            int k0 = tap_first(f), nt = tap_count(f);
-            float Tt[REF_MAX_CH];
-            for (int s = 0; s < nt; ++s) {
-                int ny = i0y + k0 + s;
-                float wy = stf_ref_weight(f, cy[lane] - (float)ny);
-                for (int t = 0; t < nt; ++t) {
-                    int nx = i0x + k0 + t;
-                    float wx = stf_ref_weight(f, cx[lane] - (float)nx);
-                    float w = wx * wy;
-                    fetch_texel(m, nx, ny, Tt);
-                    for (int c = 0; c < C; ++c) res[c] = res[c] + w * Tt[c];
-                }
-            }
+            full_filter(m, f, C, cx[lane], cy[lane], NULL, NULL, NULL, 0, res);
         } else {
             /* weighted importance sampling over the footprint (Section 4.5):
              * w_j = p_c(x_j) / p_j(x_j), result = sum w_j T_j / sum w_j */
@@ -520,6 +540,10 @@ static void render_tile(const job_t* J, int tx, int ty)
                 wsum = wsum + w;
             }
             for (int c = 0; c < C; ++c) res[c] = acc[c] / wsum;
+            /* exact filtering: every texel the pixel's own bilinear filter weighs is among the
+             * footprint's samples -> the deterministic filter over those samples */
+            if (J->exact && f == REF_BILINEAR)
+                full_filter(m, f, C, cx[lane], cy[lane], ix, iy, list, n, res);
         }
         size_t pix = (size_t)y * v->width + x;
         if (J->out_ch) for (int c = 0; c < REF_MAX_CH; ++c) J->out_ch[pix * REF_MAX_CH + c] = res[c];
@@ -589,11 +613,14 @@ int stf_ref_render(const ref_material* m, const ref_view* v, int mode, uint64_t 
                    float* out_rgba, uint32_t* out_idx, float* out_ch, int nthreads)
 {
     if (check_args(m, v) || !out_rgba) return 1;
+    const int exact = (mode & REF_FLAG_EXACT) != 0;
+    mode &= ~REF_FLAG_EXACT;
     if (mode < REF_FULL || mode > REF_WAVE4) return 1;
+    if (exact && mode < REF_QUAD2) return 1; /* exact filtering needs shared samples */
     if (mode == REF_QUAD2 && (v->tile_w % 2 || v->tile_h % 2)) return 1;
     job_t J;
     memset(&J, 0, sizeof J);
-    J.m = m; J.v = v; J.mode = mode; J.seed = seed;
+    J.m = m; J.v = v; J.mode = mode; J.exact = exact; J.seed = seed;
     J.out_rgba = out_rgba; J.out_idx = out_idx; J.out_ch = out_ch;
     return run_jobs(&J, nthreads);
 }

@@ -28,6 +28,11 @@ enum { REF_BILINEAR = 0, REF_BSPLINE3 = 1 };
 /* Sharing modes (Sections 4.3.1, 4.5; Table 1). FULL is the deterministic filter. */
 enum { REF_FULL = 0, REF_ONE_TAP = 1, REF_QUAD2 = 2, REF_WAVE2 = 3, REF_WAVE3 = 4, REF_WAVE4 = 5 };
 
+/* Exact filtering (Section "Exact Filtering"), OR'd into a sharing mode: with the bilinear filter,
+ * a pixel whose footprint samples include every texel of positive weight in its own filter
+ * returns the deterministic filter over those texels instead of the estimate. */
+#define REF_FLAG_EXACT 16
+
 /* Stored texel formats. */
 enum { REF_FP32 = 0, REF_FP16 = 1, REF_BF16 = 2, REF_E4M3 = 3, REF_UNORM8 = 4 };
 
