@@ -58,6 +58,13 @@ typedef enum {
     STF_MODE_WAVE2 = 3, STF_MODE_WAVE3 = 4, STF_MODE_WAVE4 = 5
 } stf_reuse_mode;
 
+/* Exact filtering (Section "Exact Filtering"), OR'd into a sharing mode (QUAD2 .. WAVE4): with
+ * the bilinear filter, a pixel whose footprint samples include every texel of positive weight in
+ * its own filter returns the deterministic filter over those samples (bit-identical to
+ * STF_MODE_FULL at that pixel) instead of the estimate. B-spline views ignore the flag (16 taps
+ * are rarely all drawn, Section "Exact Filtering"). With FULL or ONE_TAP: STF_ERR_INVALID_ARG. */
+#define STF_MODE_FLAG_EXACT 16
+
 /* Stored texel formats. FP16 = IEEE binary16, BF16 = bfloat16, E4M3 = OCP FP8 E4M3 ("FN"),
  * UNORM8 = q / 255. NEURAL = texels decoded by a small MLP from a latent grid (see
  * stf_decoder_*). */
@@ -144,7 +151,8 @@ stf_status stf_create_texture(const stf_texture_desc* desc, stf_texture** out);
 
 /* Renders n views (host array `views`, n >= 1) with one estimator for all of them.
  * `filter` is STF_FILTER_BILINEAR / STF_FILTER_BSPLINE3 for every view, or STF_FILTER_PER_VIEW.
- * `reuse_mode` is an stf_reuse_mode. `seed` keys the counter-based random stream (pcg4d of
+ * `reuse_mode` is an stf_reuse_mode, optionally | STF_MODE_FLAG_EXACT. `seed` keys the
+ * counter-based random stream (pcg4d of
  * Jarzynski and Olano 2020) together with each pixel's (x, y, frame, view_id).
  * Each view's texture must outlive the enqueued work. Every view is validated before anything
  * is enqueued; on STF_ERR_INVALID_ARG no output is touched. Several views are rendered by one

@@ -428,12 +428,23 @@ cudaError_t stf_launch_single(const DevView& d, int kind, int mode, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
+// A reuse mode of the C interface: an stf_reuse_mode, optionally | STF_MODE_FLAG_EXACT with a
+// sharing mode.
+stf_status stf_check_mode(int mode)
+{
+    const int base = mode & ~STF_MODE_FLAG_EXACT;
+    if (base < STF_MODE_FULL || base > STF_MODE_WAVE4) return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d", mode);
+    if ((mode & STF_MODE_FLAG_EXACT) && base < STF_MODE_QUAD2)
+        return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: exact filtering needs a sharing mode", mode);
+    return STF_OK;
+}
+
 extern "C" stf_status stf_render_views(const stf_view* views, int n, int filter, int reuse_mode, unsigned long long seed)
 {
     if (!views || n < 1) return stf_fail(STF_ERR_INVALID_ARG, "stf_render_views: need n >= 1 views");
     if (filter != STF_FILTER_BILINEAR && filter != STF_FILTER_BSPLINE3 && filter != STF_FILTER_PER_VIEW)
         return stf_fail(STF_ERR_INVALID_ARG, "filter %d", filter);
-    if (reuse_mode < STF_MODE_FULL || reuse_mode > STF_MODE_WAVE4) return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d", reuse_mode);
+    if (stf_check_mode(reuse_mode) != STF_OK) return STF_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         stf_status s = stf_validate_view(views[i], i, filter, reuse_mode);
         if (s != STF_OK) return s;

@@ -22,6 +22,7 @@ constexpr float kCoordHi = 32000.0f;
 constexpr float kPi = 3.14159265f;
 constexpr int kMaxCh = 8;
 constexpr int kWarpsPerBlock = 8;  // warps (pixel tiles in flight) per render block
+constexpr int kModeFlagExact = 16;  // STF_MODE_FLAG_EXACT of the C interface
 constexpr int kBatchMaxViews = 224; // views per persistent launch (their constants sit in a constant bank)
 
 // Material kinds with a dedicated kernel. Anything else is widened to FP32 at creation.

@@ -33,6 +33,9 @@ stf_status stf_render_batch(const stf_view* views, int n, int filter, int mode, 
 // tile shape and schedule of a view, as the multi-view scheduler resolves them (no heap use)
 void stf_resolve_view_config_nohalloc(const stf_view& v, int filter, int mode, int* tw, int* th, int* sched);
 
+// STF_OK for a valid reuse mode (optionally with STF_MODE_FLAG_EXACT), else sets the error.
+stf_status stf_check_mode(int mode);
+
 // resident blocks per SM, counted from the kernel's resources (stf_api.cu)
 cudaError_t stf_resident_blocks(const void* kernel, int threads, int dyn_bytes, int* n);
 

@@ -24,10 +24,42 @@ __device__ __forceinline__ void fetch_texel(const DevView& v, int x, int y, floa
     Mat<KIND>::fetch(v, x, y, t);
 }
 
-// One warp tile of one view. MODE: 0 full filter, 1 one-tap, 2 quad 2x2, 3..5 wave k x k.
+// Exact filtering (Section "Exact Filtering"), bilinear: `srcs` holds, per bilinear tap
+// k = 2 ky + kx, 1 + the footprint lane whose sample is that tap's texel (0: none). If every tap of
+// positive weight has one, the deterministic filter over those samples replaces the estimate,
+// summed exactly as the full-filter mode sums (y outer, FMA per channel), so such a pixel equals
+// the full filter bit for bit. REC(j, T) reads lane j's decoded channels.
+template <int C, class REC>
+__device__ __forceinline__ void exact_bilinear(const Axis<0>& ax, const Axis<0>& ay, uint32_t srcs, float (&res)[C], REC rec)
+{
+    bool all = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) all = all && (((srcs >> (8 * k)) & 0xffu) != 0u || __fmul_rn(ax.w[k & 1], ay.w[k >> 1]) == 0.0f);
+    if (!all) return;
+    float acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float wt = __fmul_rn(ax.w[k & 1], ay.w[k >> 1]);
+        const uint32_t j = (srcs >> (8 * k)) & 0xffu;
+        float T[C];
+        if (j) rec((int)j - 1, T);
+        else
+#pragma unroll
+            for (int c = 0; c < C; ++c) T[c] = 0.0f;  // a zero-weight tap nobody drew
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = fmaf(wt, T[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) res[c] = acc[c];
+}
+
+// One warp tile of one view. MODE: 0 full filter, 1 one-tap, 2 quad 2x2, 3..5 wave k x k; EX:
+// exact filtering (bilinear sharing modes only).
 // All 32 lanes execute every shuffle (off-screen lanes of a partial tile compute with
 // extrapolated coordinates and only skip the store).
-template <int KIND, int F, int MODE, int TW, int TH>
+template <int KIND, int F, int MODE, int TW, int TH, bool EX = false>
 __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane, float4* rec, float* wtab)
 {
     constexpr int C = Channels<KIND>::C;
@@ -99,6 +131,7 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
 #pragma unroll
             for (int c = 0; c < C / 2; ++c) acc[c] = make_float2(0.0f, 0.0f);
             float wsum = 0.0f;
+            uint32_t srcs = 0;  // exact filtering: per bilinear tap, 1 + a lane holding its texel
 #pragma unroll
             for (int r = 0; r < FP::KY; ++r) {
 #pragma unroll
@@ -109,6 +142,14 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
                     if constexpr (F == 0) {  // W(c - n) evaluated as the oracle does
                         wx = w_bilinear(__fsub_rn(cx, m.x));
                         wy = w_bilinear(__fsub_rn(cy, m.y));
+                        if constexpr (EX) {
+                            const uint32_t pj = __float_as_uint(m.w);
+                            const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
+                            if (((kx | ky) & ~1) == 0) {
+                                const int sh = 8 * (2 * ky + kx);
+                                srcs = (srcs & ~(0xffu << sh)) | ((uint32_t)(src + 1) << sh);
+                            }
+                        }
                     } else {
                         // the same values read from this lane's taps: lattice points outside the
                         // taps have zero weight
@@ -131,10 +172,18 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
                     wsum += wt;
                 }
             }
-            __syncwarp();  // records are rewritten by the warp's next tile
             const float inv = rcp_approx(wsum);
 #pragma unroll
             for (int c = 0; c < C / 2; ++c) { res[2 * c] = acc[c].x * inv; res[2 * c + 1] = acc[c].y * inv; }
+            if constexpr (EX && F == 0)
+                exact_bilinear<C>(ax, ay, srcs, res, [&](int j, float (&T)[C]) {
+                    const float4 t0 = rec[3 * j + 1];
+                    const float4 t1 = C > 4 ? rec[3 * j + 2] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    const float tt[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+                    for (int c = 0; c < C; ++c) T[c] = tt[c];
+                });
+            __syncwarp();  // records are rewritten by the warp's next tile
         }
     }
 
@@ -165,7 +214,7 @@ constexpr int kRecPerLane = 3;
 constexpr int kMinBlocks = 5;
 
 // One view: block (bx, by) holds 8 warps on tile row by, tiles bx * 8 .. bx * 8 + 7.
-template <int KIND, int F, int MODE, int TW, int TH>
+template <int KIND, int F, int MODE, int TW, int TH, bool EX = false>
 __global__ void __launch_bounds__(256, kMinBlocks) k_render_view(const DevView v)
 {
     __shared__ float4 recs[kWarpsPerBlock * 32 * kRecPerLane];
@@ -173,7 +222,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_render_view(const DevView v
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = blockIdx.x * kWarpsPerBlock + warp;
     if (tx >= v.tiles_x) return;  // warp-uniform
-    render_tile<KIND, F, MODE, TW, TH>(v, tx, blockIdx.y, lane, recs + warp * 32 * kRecPerLane, wtabs + warp * 32 * 8);
+    render_tile<KIND, F, MODE, TW, TH, EX>(v, tx, blockIdx.y, lane, recs + warp * 32 * kRecPerLane, wtabs + warp * 32 * 8);
 }
 
 }  // namespace stf

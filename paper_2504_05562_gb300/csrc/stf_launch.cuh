@@ -37,7 +37,7 @@ static int device_sms()
     return n > 0 ? n : 1;
 }
 
-template <int KIND, int F, int MODE, int TW, int TH>
+template <int KIND, int F, int MODE, int TW, int TH, bool EX = false>
 static cudaError_t launch_one(const DevView& v, cudaStream_t s)
 {
     const dim3 grid((unsigned)((v.tiles_x + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)v.tiles_y);
@@ -46,40 +46,51 @@ static cudaError_t launch_one(const DevView& v, cudaStream_t s)
         static int cached = 0;
         int per_sm = 1;
         constexpr int dyn = (int)sizeof(NnPipeSmem);
-        cudaError_t e = prepare_dynamic(k_render_neural<F, MODE, TW, TH>, dyn, kNnPipeThreads, cached, &per_sm);
+        cudaError_t e = prepare_dynamic(k_render_neural<F, MODE, TW, TH, EX>, dyn, kNnPipeThreads, cached, &per_sm);
         if (e != cudaSuccess) return e;
         const long long groups = (long long)((v.tiles_x + kNnClientWarps - 1) / kNnClientWarps) * v.tiles_y;
         const unsigned blocks = (unsigned)(groups < (long long)per_sm * device_sms() ? groups : (long long)per_sm * device_sms());
-        k_render_neural<F, MODE, TW, TH><<<blocks, kNnPipeThreads, dyn, s>>>(v);
+        k_render_neural<F, MODE, TW, TH, EX><<<blocks, kNnPipeThreads, dyn, s>>>(v);
     } else {
-        k_render_view<KIND, F, MODE, TW, TH><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
+        k_render_view<KIND, F, MODE, TW, TH, EX><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
     }
     return cudaGetLastError();
 }
 
-template <int KIND, int F, int MODE>
+template <int KIND, int F, int MODE, bool EX>
 static cudaError_t launch_tiles(const DevView& v, cudaStream_t s)
 {
-    if (v.tile_w == 8 && v.tile_h == 4) return launch_one<KIND, F, MODE, 8, 4>(v, s);
-    if (v.tile_w == 4 && v.tile_h == 8) return launch_one<KIND, F, MODE, 4, 8>(v, s);
-    if (v.tile_w == 16 && v.tile_h == 2) return launch_one<KIND, F, MODE, 16, 2>(v, s);
+    if (v.tile_w == 8 && v.tile_h == 4) return launch_one<KIND, F, MODE, 8, 4, EX>(v, s);
+    if (v.tile_w == 4 && v.tile_h == 8) return launch_one<KIND, F, MODE, 4, 8, EX>(v, s);
+    if (v.tile_w == 16 && v.tile_h == 2) return launch_one<KIND, F, MODE, 16, 2, EX>(v, s);
     return cudaErrorInvalidValue;
+}
+
+// Sharing modes; exact filtering exists for the bilinear filter (the B-spline ignores the flag).
+template <int KIND, int F, int MODE>
+static cudaError_t launch_sharing(const DevView& v, bool ex, cudaStream_t s)
+{
+    if constexpr (F == 0)
+        if (ex) return launch_tiles<KIND, F, MODE, true>(v, s);
+    return launch_tiles<KIND, F, MODE, false>(v, s);
 }
 
 template <int KIND, int F>
 static cudaError_t launch_modes(const DevView& v, int mode, cudaStream_t s)
 {
-    switch (mode) {
+    const bool ex = (mode & kModeFlagExact) != 0;
+    switch (mode & ~kModeFlagExact) {
     case 0: return launch_one<KIND, F, 0, 8, 4>(v, s);  // no sharing: tile shape irrelevant
     case 1: return launch_one<KIND, F, 1, 8, 4>(v, s);
-    case 2: return launch_tiles<KIND, F, 2>(v, s);
-    case 3: return launch_tiles<KIND, F, 3>(v, s);
-    case 4: return launch_tiles<KIND, F, 4>(v, s);
-    case 5: return launch_tiles<KIND, F, 5>(v, s);
+    case 2: return launch_sharing<KIND, F, 2>(v, ex, s);
+    case 3: return launch_sharing<KIND, F, 3>(v, ex, s);
+    case 4: return launch_sharing<KIND, F, 4>(v, ex, s);
+    case 5: return launch_sharing<KIND, F, 5>(v, ex, s);
     }
     return cudaErrorInvalidValue;
 }
 
+// mode: the C interface's reuse mode, with STF_MODE_FLAG_EXACT (kModeFlagExact) allowed.
 template <int KIND>
 cudaError_t launch_view_kind(const DevView& v, int mode, cudaStream_t s)
 {
@@ -97,7 +108,7 @@ static __constant__ DevView c_batch_views[kBatchMaxViews];
 // (a run of tiles of one view) from a device counter until the list is exhausted. Nothing waits
 // on another block, so no wait can stall. One kernel per variant keeps the code of a launch as
 // small as a single-view kernel's.
-template <int KIND, int MODE, int F, int TW, int TH>
+template <int KIND, int MODE, int F, int TW, int TH, bool EX = false>
 __global__ void __launch_bounds__(256, kMinBlocks)
     k_render_batch(const WorkItem* __restrict__ items, int n_items, int* counter)
 {
@@ -120,7 +131,7 @@ __global__ void __launch_bounds__(256, kMinBlocks)
         for (int k = warp; k < w.ntiles; k += kWarpsPerBlock) {
             const int t = w.tile0 + k;
             const int ty = t / v.tiles_x;
-            render_tile<KIND, F, MODE, TW, TH>(v, t - ty * v.tiles_x, ty, lane, rec, wtab);
+            render_tile<KIND, F, MODE, TW, TH, EX>(v, t - ty * v.tiles_x, ty, lane, rec, wtab);
         }
     }
 }
@@ -132,7 +143,7 @@ struct NnConstViews {
 // The neural kind's multi-view kernel: the same work items, rendered by the client warps of the
 // decode pipeline (all of a batch's neural views share one decoder; view 0 names it). The client
 // warps pull items together (named barrier 1), so every client takes the same rounds.
-template <int MODE, int F, int TW, int TH>
+template <int MODE, int F, int TW, int TH, bool EX = false>
 __global__ void __launch_bounds__(kNnPipeThreads, 2)
     k_render_neural_batch(const WorkItem* __restrict__ items, int n_items, int* counter)
 {
@@ -145,7 +156,7 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2)
         nn_decode_role(sm, c_batch_views[0].flags);
     } else {
         const int warp = threadIdx.x >> 5;
-        NnRenderClient<F, MODE, TW, TH, NnConstViews> cl(sm, wtabs + warp * 256, NnConstViews{}, c_batch_views[0].flags);
+        NnRenderClient<F, MODE, TW, TH, EX, NnConstViews> cl(sm, wtabs + warp * 256, NnConstViews{}, c_batch_views[0].flags);
 #pragma unroll 1
         for (;;) {
             if (threadIdx.x == 0) {
@@ -173,27 +184,29 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2)
 }
 
 // grid > 0 launches; grid == 0 only reports the instance's resident blocks per SM in *per_sm.
-template <int KIND, int MODE, int F, int TW, int TH>
+template <int KIND, int MODE, int F, int TW, int TH, bool EX = false>
 static cudaError_t launch_batch_v(const WorkItem* items, int n_items, int* counter, int grid, int* per_sm, cudaStream_t s)
 {
     if constexpr (KIND == K_NEURAL) {
         static int cached = 0;
         constexpr int dyn = (int)sizeof(NnPipeSmem);
         int n = 0;
-        cudaError_t e = prepare_dynamic(k_render_neural_batch<MODE, F, TW, TH>, dyn, kNnPipeThreads, cached, &n);
+        cudaError_t e = prepare_dynamic(k_render_neural_batch<MODE, F, TW, TH, EX>, dyn, kNnPipeThreads, cached, &n);
         if (e != cudaSuccess || grid == 0) {
             *per_sm = n;
             return e;
         }
-        k_render_neural_batch<MODE, F, TW, TH><<<grid, kNnPipeThreads, dyn, s>>>(items, n_items, counter);
+        k_render_neural_batch<MODE, F, TW, TH, EX><<<grid, kNnPipeThreads, dyn, s>>>(items, n_items, counter);
     } else {
-        if (grid == 0) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE, F, TW, TH>, 256, 0);
-        k_render_batch<KIND, MODE, F, TW, TH><<<grid, 256, 0, s>>>(items, n_items, counter);
+        if (grid == 0)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE, F, TW, TH, EX>, 256, 0);
+        k_render_batch<KIND, MODE, F, TW, TH, EX><<<grid, 256, 0, s>>>(items, n_items, counter);
     }
     return cudaGetLastError();
 }
 
-// variant = filter * 3 + tile shape (0: 8x4, 1: 4x8, 2: 16x2); without sharing only 8x4 exists.
+// variant = filter * 3 + tile shape (0: 8x4, 1: 4x8, 2: 16x2), + 6 for bilinear with exact
+// filtering; without sharing only 8x4 exists.
 template <int KIND, int MODE>
 static cudaError_t launch_batch_mode(const WorkItem* items, int n_items, int* counter, int grid, int variant, int* per_sm,
                                      cudaStream_t s)
@@ -210,6 +223,9 @@ static cudaError_t launch_batch_mode(const WorkItem* items, int n_items, int* co
         case 3: return launch_batch_v<KIND, MODE, 1, 8, 4>(items, n_items, counter, grid, per_sm, s);
         case 4: return launch_batch_v<KIND, MODE, 1, 4, 8>(items, n_items, counter, grid, per_sm, s);
         case 5: return launch_batch_v<KIND, MODE, 1, 16, 2>(items, n_items, counter, grid, per_sm, s);
+        case 6: return launch_batch_v<KIND, MODE, 0, 8, 4, true>(items, n_items, counter, grid, per_sm, s);
+        case 7: return launch_batch_v<KIND, MODE, 0, 4, 8, true>(items, n_items, counter, grid, per_sm, s);
+        case 8: return launch_batch_v<KIND, MODE, 0, 16, 2, true>(items, n_items, counter, grid, per_sm, s);
         }
         return cudaErrorInvalidValue;
     }
@@ -219,7 +235,7 @@ template <int KIND>
 cudaError_t launch_batch_kind(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant,
                               int* per_sm, cudaStream_t s)
 {
-    switch (mode) {
+    switch (mode & ~kModeFlagExact) {  // the flag is in the variant
     case 0: return launch_batch_mode<KIND, 0>(items, n_items, counter, grid, variant, per_sm, s);
     case 1: return launch_batch_mode<KIND, 1>(items, n_items, counter, grid, variant, per_sm, s);
     case 2: return launch_batch_mode<KIND, 2>(items, n_items, counter, grid, variant, per_sm, s);

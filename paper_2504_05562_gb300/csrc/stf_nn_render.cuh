@@ -15,6 +15,7 @@
 #include <float.h>
 
 #include "stf_device.cuh"
+#include "stf_kernels.cuh"
 #include "stf_neural.cuh"
 
 namespace stf {
@@ -23,8 +24,9 @@ namespace stf {
 constexpr int kNnWtabFloats = kNnClientWarps * 32 * 8;
 
 // The client side of one block. VIEWS maps a view index to its constants (a kernel parameter or
-// the batch's constant bank). Every client thread calls round() for the same rounds.
-template <int F, int MODE, int TW, int TH, class VIEWS>
+// the batch's constant bank). Every client thread calls round() for the same rounds. EX: exact
+// filtering (bilinear sharing modes).
+template <int F, int MODE, int TW, int TH, bool EX, class VIEWS>
 struct NnRenderClient {
     static constexpr int NT = MODE == 0 ? Taps<F>::N * Taps<F>::N : 1;  // rounds per tile group
     NnPipeSmem& sm;
@@ -121,6 +123,10 @@ struct NnRenderClient {
             pixel_uv(v, x, y, u, wv);
             const float cx = texel_coord(u, v.tex_wf), cy = texel_coord(wv, v.tex_hf);
             Axis<F> ax, ay;
+            if constexpr (F == 0 && EX) {
+                axis_weights<F>(cx, ax);
+                axis_weights<F>(cy, ay);
+            }
             if constexpr (F == 1) {
                 axis_weights<F>(cx, ax);
                 axis_weights<F>(cy, ay);
@@ -134,6 +140,7 @@ struct NnRenderClient {
 #pragma unroll
             for (int c = 0; c < 4; ++c) a2[c] = make_float2(0.0f, 0.0f);
             float wsum = 0.0f;
+            uint32_t srcs = 0;  // exact filtering: per bilinear tap, 1 + a lane holding its texel
 #pragma unroll
             for (int rr2 = 0; rr2 < FP::KY; ++rr2) {
 #pragma unroll
@@ -144,6 +151,14 @@ struct NnRenderClient {
                     if constexpr (F == 0) {
                         wx = w_bilinear(__fsub_rn(cx, m.x));
                         wy = w_bilinear(__fsub_rn(cy, m.y));
+                        if constexpr (EX) {
+                            const uint32_t pj = __float_as_uint(m.w);
+                            const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
+                            if (((kx | ky) & ~1) == 0) {
+                                const int sh = 8 * (2 * ky + kx);
+                                srcs = (srcs & ~(0xffu << sh)) | ((uint32_t)(src + 1) << sh);
+                            }
+                        }
                     } else {
                         const uint32_t pj = __float_as_uint(m.w);
                         const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
@@ -166,6 +181,8 @@ struct NnRenderClient {
             const float inv = rcp_approx(wsum);
 #pragma unroll
             for (int c = 0; c < 4; ++c) { res[2 * c] = a2[c].x * inv; res[2 * c + 1] = a2[c].y * inv; }
+            if constexpr (EX && F == 0)
+                exact_bilinear<8>(ax, ay, srcs, res, [&](int j, float (&T)[8]) { nn_get_outputs(sm, slot, row0 + j, T); });
         }
         if (x < v.width && y < v.height) {
             float u, wv;
@@ -216,7 +233,7 @@ struct NnParamView {
 };
 
 // One view: persistent blocks walk the view's tile groups (kNnClientWarps tiles of one tile row).
-template <int F, int MODE, int TW, int TH>
+template <int F, int MODE, int TW, int TH, bool EX = false>
 __global__ void __launch_bounds__(kNnPipeThreads, 2) k_render_neural(const __grid_constant__ DevView v)
 {
     extern __shared__ __align__(128) unsigned char dyn[];
@@ -227,7 +244,7 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2) k_render_neural(const __gri
         nn_decode_role(sm, v.flags);
     } else {
         const int warp = threadIdx.x >> 5;
-        NnRenderClient<F, MODE, TW, TH, NnParamView> cl(sm, wtabs + warp * 256, NnParamView{&v}, v.flags);
+        NnRenderClient<F, MODE, TW, TH, EX, NnParamView> cl(sm, wtabs + warp * 256, NnParamView{&v}, v.flags);
         const int gx = (v.tiles_x + kNnClientWarps - 1) / kNnClientWarps;
         const int groups = gx * v.tiles_y;
 #pragma unroll 1

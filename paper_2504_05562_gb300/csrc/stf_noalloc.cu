@@ -42,7 +42,7 @@ STF_DECLARE_BATCH_NA(launch_view_NEURAL)
 
 namespace {
 
-constexpr int kVariants = 6;
+constexpr int kVariants = 9;  // filter * 3 + tile, 6 + tile for bilinear with exact filtering
 
 struct NoallocScratch {
     DevView views[STF_NOALLOC_MAX_VIEWS];
@@ -124,7 +124,7 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
                         n, STF_NOALLOC_MAX_VIEWS);
     if (filter != STF_FILTER_BILINEAR && filter != STF_FILTER_BSPLINE3 && filter != STF_FILTER_PER_VIEW)
         return stf_fail(STF_ERR_INVALID_ARG, "filter %d", filter);
-    if (reuse_mode < STF_MODE_FULL || reuse_mode > STF_MODE_WAVE4) return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d", reuse_mode);
+    if (stf_check_mode(reuse_mode) != STF_OK) return STF_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         stf_status s = stf_validate_view(views[i], i, filter, reuse_mode);
         if (s != STF_OK) return s;
@@ -187,7 +187,9 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
             d.tile_h = th[i];
             d.tiles_x = (d.width + tw[i] - 1) / tw[i];
             d.tiles_y = (d.height + th[i] - 1) / th[i];
-            var_of[j] = (filter == STF_FILTER_PER_VIEW ? views[i].filter : filter) * 3 + (tw[i] == 8 ? 0 : (tw[i] == 4 ? 1 : 2));
+            const int f = filter == STF_FILTER_PER_VIEW ? views[i].filter : filter;
+            const int tc = tw[i] == 8 ? 0 : (tw[i] == 4 ? 1 : 2);
+            var_of[j] = (reuse_mode & STF_MODE_FLAG_EXACT) && f == STF_FILTER_BILINEAR ? 6 + tc : f * 3 + tc;
         }
         // items of the group, contiguous per variant (one persistent kernel per variant)
         for (int var = 0; var < kVariants; ++var) {

@@ -243,7 +243,9 @@ void build_groups(const stf_view* views, int n, int filter, int mode, std::vecto
             resolve(v, filter, mode, &tw, &th, &sc);
             const int tiles = ((v.width + tw - 1) / tw) * ((v.height + th - 1) / th);
             const int per = kWarpsPerBlock * sc;
-            const int variant = view_filter(v, filter) * 3 + tile_code(tw, th);
+            const int f = view_filter(v, filter);
+            const bool ex = (mode & STF_MODE_FLAG_EXACT) && f == STF_FILTER_BILINEAR;
+            const int variant = ex ? 6 + tile_code(tw, th) : f * 3 + tile_code(tw, th);
             Sub* sub = nullptr;
             for (Sub& x : g.subs)
                 if (x.variant == variant) sub = &x;
@@ -421,7 +423,7 @@ extern "C" stf_status stf_view_config(const stf_view* view, int filter, int reus
 extern "C" stf_status stf_autotune(const stf_view* views, int n, int filter, int reuse_mode, unsigned long long seed)
 {
     if (!views || n < 1) return stf_fail(STF_ERR_INVALID_ARG, "stf_autotune: need n >= 1 views");
-    if (reuse_mode < STF_MODE_FULL || reuse_mode > STF_MODE_WAVE4) return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d", reuse_mode);
+    if (stf_check_mode(reuse_mode) != STF_OK) return STF_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         stf_status s = stf_validate_view(views[i], i, filter, reuse_mode);
         if (s != STF_OK) return s;

@@ -16,6 +16,7 @@ from . import build as _build
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_ASSERT = range(7)
 FILTER_BILINEAR, FILTER_BSPLINE3, FILTER_PER_VIEW = 0, 1, -1
 MODE_FULL, MODE_ONE_TAP, MODE_QUAD2, MODE_WAVE2, MODE_WAVE3, MODE_WAVE4 = range(6)
+MODE_FLAG_EXACT = 16  # exact filtering (bilinear), OR'd into a sharing mode
 FMT_FP32, FMT_FP16, FMT_BF16, FMT_E4M3, FMT_UNORM8, FMT_NEURAL = range(6)
 MODE_NAMES = {"full": 0, "one_tap": 1, "quad2": 2, "wave2": 3, "wave3": 4, "wave4": 5}
 

@@ -46,6 +46,10 @@ def test_invalid_arguments_rejected_on_host():
     assert "null texture" in stf.last_error()
     assert L.stf_render_views(arr, 1, 7, 4, 0) == stf.ERR_INVALID_ARG  # bad filter
     assert L.stf_render_views(arr, 1, 0, 9, 0) == stf.ERR_INVALID_ARG  # bad mode
+    for mode in (stf.MODE_FULL, stf.MODE_ONE_TAP):  # exact filtering needs a sharing mode
+        assert L.stf_render_views(arr, 1, 0, mode | stf.MODE_FLAG_EXACT, 0) == stf.ERR_INVALID_ARG
+        assert "exact filtering" in stf.last_error()
+    assert L.stf_render_views(arr, 1, 0, 9 | stf.MODE_FLAG_EXACT, 0) == stf.ERR_INVALID_ARG
     assert L.stf_create_texture(None, None) == stf.ERR_INVALID_ARG
     d = stf.TextureDesc()
     d.width, d.height, d.num_planes = 0, 4, 1

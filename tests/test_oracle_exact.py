@@ -2,48 +2,15 @@
 
 With the bilinear filter, a pixel whose footprint samples include every texel its own filter
 weighs (positive weight) returns the deterministic filter over those texels; every other pixel
-returns the weighted-importance estimate. The pixels that qualify are found here independently
-of the oracle's branch, from its sampled texel indices and footprints.
+returns the weighted-importance estimate. The pixels that qualify are found independently of the
+oracle's branch (exact_support.py), from its sampled texel indices and footprints.
 """
 import numpy as np
 import pytest
 
 import oracle as O
+from exact_support import qualifying
 from paper_2504_05562_gb300 import workloads as W
-
-
-def _qualifying(view, mat, idx, mode):
-    """Pixels whose bilinear support (positive-weight taps) is covered by the footprint's samples."""
-    tw, th = view["tile"]
-    h, w = view["height"], view["width"]
-    ok = np.zeros((h, w), bool)
-    ix = (idx & 0xFFFF).astype(np.int64)
-    ix = np.where(ix >= 0x8000, ix - 0x10000, ix)
-    iy = (idx >> 16).astype(np.int64)
-    iy = np.where(iy >= 0x8000, iy - 0x10000, iy)
-    for ty in range(0, h, th):
-        for tx in range(0, w, tw):
-            for lane in range(32):
-                x, y = tx + lane % tw, ty + lane // tw
-                if x >= w or y >= h:
-                    continue
-                cx, cy = O.texel_coords(view, mat["width"], mat["height"], x, y)
-                samples = set()
-                for j in O.footprint(mode, tw, th, lane):
-                    sx, sy = tx + j % tw, ty + j // tw
-                    assert sx < w and sy < h  # whole tiles: every footprint lane is on screen
-                    samples.add((ix[sy, sx], iy[sy, sx]))
-                need = []
-                cx32, cy32 = np.float32(cx), np.float32(cy)
-                x0, y0 = int(np.floor(cx32)), int(np.floor(cy32))
-                for ny in (y0, y0 + 1):
-                    for nx in (x0, x0 + 1):
-                        wx = O.weight(O.BILINEAR, float(cx32 - np.float32(nx)))  # FP32 differences, as the method
-                        wy = O.weight(O.BILINEAR, float(cy32 - np.float32(ny)))
-                        if np.float32(wx) * np.float32(wy) > 0:
-                            need.append((nx, ny))
-                ok[y, x] = all(t in samples for t in need)
-    return ok
 
 
 @pytest.mark.parametrize("mode", [O.QUAD2, O.WAVE2, O.WAVE3, O.WAVE4])
@@ -54,7 +21,7 @@ def test_exact_pixels_equal_full_filter_bitwise_others_the_estimate(mode):
     wis, idx, _ = O.render(mat, view, mode, seed=3)
     ex, idx2, _ = O.render(mat, view, mode | O.FLAG_EXACT, seed=3)
     assert np.array_equal(idx, idx2)  # the same selections
-    q = _qualifying(view, mat, idx, mode)
+    q = qualifying(view, mat["width"], mat["height"], idx, mode)
     assert q.any() and not q.all()
     assert np.array_equal(ex[q], full[q])
     assert np.array_equal(ex[~q], wis[~q])
