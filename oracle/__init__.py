@@ -26,6 +26,12 @@ LIB = os.path.join(HERE, "_build", "liboracle.so")
 BILINEAR, BSPLINE3 = 0, 1
 FULL, ONE_TAP, QUAD2, WAVE2, WAVE3, WAVE4 = 0, 1, 2, 3, 4, 5
 FLAG_EXACT = 16  # exact filtering (bilinear), OR'd into a sharing mode
+EST_SHIFT, FLAG_CLAMP = 8, 2048  # alternative estimators: mode | (est << EST_SHIFT) [| FLAG_CLAMP]
+EST_WIS, EST_IS, EST_MIS, EST_PMIS, EST_REG = range(5)
+
+
+def est_mode(mode, est, clamp=False):
+    return mode | (est << EST_SHIFT) | (FLAG_CLAMP if clamp else 0)
 FP32, FP16, BF16, E4M3, UNORM8 = 0, 1, 2, 3, 4
 
 _lock = threading.Lock()

@@ -447,6 +447,7 @@ typedef struct {
     const ref_view* v;
     int mode;                /* sharing mode without flags */
     int exact;               /* REF_FLAG_EXACT given */
+    int est, clamp;          /* REF_EST_*, REF_FLAG_CLAMP given */
     uint64_t seed;
     float* out_rgba;
     uint32_t* out_idx;
@@ -494,6 +495,97 @@ static int full_filter(const ref_material* m, int f, int C, float cx, float cy, 
     return 1;
 }
 
+/* Lane j's filter weight (its PMF) at texel (nx, ny). */
+static float pmf_at(int f, const float* cx, const float* cy, int j, int nx, int ny)
+{
+    return stf_ref_weight(f, cx[j] - (float)nx) * stf_ref_weight(f, cy[j] - (float)ny);
+}
+
+/* The alternative estimators of the pixel of lane c over its footprint samples list[0..n)
+ * (see REF_EST_* in the header), each sum in list order. */
+static void alt_estimate(int est, int clamp, int f, int C, int c, const float* cx, const float* cy, const int* ix,
+                         const int* iy, const float* p, const float (*T)[REF_MAX_CH], const int* list, int n,
+                         float* res)
+{
+    float acc[REF_MAX_CH] = {0};
+    const float nf = (float)n;
+    if (est == REF_EST_IS) {
+        for (int i = 0; i < n; ++i) {
+            int j = list[i];
+            float r = pmf_at(f, cx, cy, c, ix[j], iy[j]) / p[j];
+            for (int k = 0; k < C; ++k) acc[k] = acc[k] + r * T[j][k];
+        }
+        for (int k = 0; k < C; ++k) res[k] = acc[k] / nf;
+    } else if (est == REF_EST_MIS) {
+        for (int i = 0; i < n; ++i) {
+            int j = list[i];
+            float den = 0.0f;
+            for (int q = 0; q < n; ++q) den = den + pmf_at(f, cx, cy, list[q], ix[j], iy[j]);
+            float r = pmf_at(f, cx, cy, c, ix[j], iy[j]) / den;
+            for (int k = 0; k < C; ++k) acc[k] = acc[k] + r * T[j][k];
+        }
+        for (int k = 0; k < C; ++k) res[k] = acc[k];
+    } else if (est == REF_EST_PMIS) {
+        const float m1 = nf - 1.0f;
+        for (int i = 0; i < n; ++i) {
+            int j = list[i];
+            float pc = pmf_at(f, cx, cy, c, ix[j], iy[j]);
+            float r;
+            if (j == c) {
+                /* canonical: m_c(x_c) f(x_c)/p_c(x_c) = m_c(x_c) T_c */
+                float mc = 0.0f;
+                for (int q = 0; q < n; ++q) {
+                    if (list[q] == c) continue;
+                    float pj = pmf_at(f, cx, cy, list[q], ix[j], iy[j]);
+                    mc = mc + pc / (pc + m1 * pj);
+                }
+                r = mc / m1;
+            } else {
+                /* m_i(x_i) f(x_i)/p_i(x_i) = p_c(x_i) T_i / (p_c(x_i) + (n-1) p_i(x_i)) */
+                r = pc / (pc + m1 * p[j]);
+            }
+            for (int k = 0; k < C; ++k) acc[k] = acc[k] + r * T[j][k];
+        }
+        for (int k = 0; k < C; ++k) res[k] = acc[k];
+    } else { /* REF_EST_REG */
+        float h[16], hbar = 0.0f;
+        for (int i = 0; i < n; ++i) {
+            int j = list[i];
+            h[i] = pmf_at(f, cx, cy, c, ix[j], iy[j]) / p[j];
+            hbar = hbar + h[i];
+        }
+        hbar = hbar / nf;
+        float shh = 0.0f;
+        for (int i = 0; i < n; ++i) {
+            float d = h[i] - hbar;
+            shh = shh + d * d;
+        }
+        for (int k = 0; k < C; ++k) {
+            float sy = 0.0f, shy = 0.0f;
+            for (int i = 0; i < n; ++i) {
+                float y = h[i] * T[list[i]][k];
+                sy = sy + y;
+                shy = shy + (h[i] - hbar) * y;
+            }
+            float beta = shh > 0.0f ? shy / shh : 0.0f;
+            res[k] = sy / nf - beta * (hbar - 1.0f);
+        }
+    }
+    if (clamp) {
+        for (int k = 0; k < C; ++k) {
+            float lo = INFINITY, hi = -INFINITY;
+            for (int i = 0; i < n; ++i) {
+                int j = list[i];
+                if (pmf_at(f, cx, cy, c, ix[j], iy[j]) > 0.0f) {
+                    lo = fminf(lo, T[j][k]);
+                    hi = fmaxf(hi, T[j][k]);
+                }
+            }
+            res[k] = fminf(fmaxf(res[k], lo), hi);
+        }
+    }
+}
+
 static void render_tile(const job_t* J, int tx, int ty)
 {
     const ref_material* m = J->m;
@@ -525,6 +617,10 @@ static void render_tile(const job_t* J, int tx, int ty)
         if (J->mode == REF_FULL) {
             /* deterministic filter: sum over the lattice taps of W(dx) W(dy) T, y outer */
             full_filter(m, f, C, cx[lane], cy[lane], NULL, NULL, NULL, 0, res);
+        } else if (J->est != REF_EST_WIS) {
+            int list[16];
+            int n = stf_ref_footprint(J->mode, tw, th, lane, list);
+            alt_estimate(J->est, J->clamp, f, C, lane, cx, cy, ix, iy, p, (const float(*)[REF_MAX_CH])T, list, n, res);
         } else {
             /* weighted importance sampling over the footprint (Section 4.5):
              * w_j = p_c(x_j) / p_j(x_j), result = sum w_j T_j / sum w_j */
@@ -614,13 +710,17 @@ int stf_ref_render(const ref_material* m, const ref_view* v, int mode, uint64_t 
 {
     if (check_args(m, v) || !out_rgba) return 1;
     const int exact = (mode & REF_FLAG_EXACT) != 0;
-    mode &= ~REF_FLAG_EXACT;
+    const int est = (mode >> REF_EST_SHIFT) & 7;
+    const int clamp = (mode & REF_FLAG_CLAMP) != 0;
+    mode &= 15;
     if (mode < REF_FULL || mode > REF_WAVE4) return 1;
     if (exact && mode < REF_QUAD2) return 1; /* exact filtering needs shared samples */
+    if ((est != REF_EST_WIS || clamp) && mode < REF_QUAD2) return 1;
+    if (est > REF_EST_REG || (clamp && est == REF_EST_WIS) || (exact && est != REF_EST_WIS)) return 1;
     if (mode == REF_QUAD2 && (v->tile_w % 2 || v->tile_h % 2)) return 1;
     job_t J;
     memset(&J, 0, sizeof J);
-    J.m = m; J.v = v; J.mode = mode; J.exact = exact; J.seed = seed;
+    J.m = m; J.v = v; J.mode = mode; J.exact = exact; J.est = est; J.clamp = clamp; J.seed = seed;
     J.out_rgba = out_rgba; J.out_idx = out_idx; J.out_ch = out_ch;
     return run_jobs(&J, nthreads);
 }

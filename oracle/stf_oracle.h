@@ -33,6 +33,24 @@ enum { REF_FULL = 0, REF_ONE_TAP = 1, REF_QUAD2 = 2, REF_WAVE2 = 3, REF_WAVE3 = 
  * returns the deterministic filter over those texels instead of the estimate. */
 #define REF_FLAG_EXACT 16
 
+/* The estimator of a sharing mode, (mode >> REF_EST_SHIFT) & 7 (Section 4.1 and Section 4.2),
+ * over the footprint's samples x_i drawn from the PMFs p_i (lane i's filter weights), with
+ * f(x) = w_c(x) T(x) for the pixel's own filter w_c:
+ *   WIS   sum_i (w_c(x_i)/p_i(x_i)) T_i / sum_i w_c(x_i)/p_i(x_i)   (the paper's estimator; default)
+ *   IS    (1/n) sum_i f(x_i)/p_i(x_i)                                 (Eq. eq_basic_mc)
+ *   MIS   sum_i f(x_i) / sum_k p_k(x_i)                               (balance heuristic)
+ *   PMIS  pairwise MIS with the pixel's own sample as the canonical technique (Bitterli 2022):
+ *         m_c(x) = 1/(n-1) sum_{j!=c} p_c(x)/(p_c(x) + (n-1) p_j(x)),
+ *         m_i(x) = p_i(x)/(p_c(x) + (n-1) p_i(x)) (i != c), F = sum_i m_i(x_i) f(x_i)/p_i(x_i)
+ *   REG   regression (control variate h = w_c/p with mean 1; Owen 2013, Eq. 9.11):
+ *         y_i = f(x_i)/p_i(x_i), h_i = w_c(x_i)/p_i(x_i), beta = sum (h_i - hbar) y_i / sum (h_i - hbar)^2
+ *         (0 if the denominator is 0), F = ybar - beta (hbar - 1)      (Eq. eq_mc_regression)
+ * REF_FLAG_CLAMP clamps each channel of a non-WIS estimate to the range of the texels with
+ * w_c > 0 among the samples (Section 4.1). */
+#define REF_EST_SHIFT 8
+enum { REF_EST_WIS = 0, REF_EST_IS = 1, REF_EST_MIS = 2, REF_EST_PMIS = 3, REF_EST_REG = 4 };
+#define REF_FLAG_CLAMP 2048
+
 /* Stored texel formats. */
 enum { REF_FP32 = 0, REF_FP16 = 1, REF_BF16 = 2, REF_E4M3 = 3, REF_UNORM8 = 4 };
 
