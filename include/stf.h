@@ -65,6 +65,25 @@ typedef enum {
  * are rarely all drawn, Section "Exact Filtering"). With FULL or ONE_TAP: STF_ERR_INVALID_ARG. */
 #define STF_MODE_FLAG_EXACT 16
 
+/* The estimator of a sharing mode, reuse_mode | (estimator << STF_MODE_EST_SHIFT), over the
+ * footprint's samples x_i (drawn from the PMFs p_i = lane i's filter weights), with
+ * f(x) = w_c(x) T(x) for the pixel's own filter w_c (Section 4.1 and Section 4.2):
+ *   STF_EST_WIS           the paper's weighted estimator (default)
+ *   STF_EST_IS            importance sampling, (1/n) sum f(x_i)/p_i(x_i)  (Eq. eq_basic_mc)
+ *   STF_EST_MIS           balance heuristic, sum f(x_i) / sum_k p_k(x_i)
+ *   STF_EST_PAIRWISE_MIS  pairwise MIS with the pixel's own sample as the canonical technique
+ *   STF_EST_REGRESSION    control variate h = w_c/p (mean 1), y = f/p, beta from the samples
+ *                         (Eq. eq_mc_regression)
+ * STF_MODE_FLAG_CLAMP clamps a non-weighted estimate per channel to the range of the sampled
+ * texels its own filter weighs. These are evaluation modes for the estimator comparison: one
+ * view per call, stored material kinds, 8x4 tiles, no exact filtering; anything else
+ * STF_ERR_INVALID_ARG. */
+#define STF_MODE_EST_SHIFT 8
+typedef enum {
+    STF_EST_WIS = 0, STF_EST_IS = 1, STF_EST_MIS = 2, STF_EST_PAIRWISE_MIS = 3, STF_EST_REGRESSION = 4
+} stf_estimator;
+#define STF_MODE_FLAG_CLAMP 2048
+
 /* Stored texel formats. FP16 = IEEE binary16, BF16 = bfloat16, E4M3 = OCP FP8 E4M3 ("FN"),
  * UNORM8 = q / 255. NEURAL = texels decoded by a small MLP from a latent grid (see
  * stf_decoder_*). */
@@ -151,7 +170,8 @@ stf_status stf_create_texture(const stf_texture_desc* desc, stf_texture** out);
 
 /* Renders n views (host array `views`, n >= 1) with one estimator for all of them.
  * `filter` is STF_FILTER_BILINEAR / STF_FILTER_BSPLINE3 for every view, or STF_FILTER_PER_VIEW.
- * `reuse_mode` is an stf_reuse_mode, optionally | STF_MODE_FLAG_EXACT. `seed` keys the
+ * `reuse_mode` is an stf_reuse_mode, optionally | STF_MODE_FLAG_EXACT or an estimator
+ * (STF_MODE_EST_SHIFT, STF_MODE_FLAG_CLAMP). `seed` keys the
  * counter-based random stream (pcg4d of
  * Jarzynski and Olano 2020) together with each pixel's (x, y, frame, view_id).
  * Each view's texture must outlive the enqueued work. Every view is validated before anything

@@ -368,7 +368,7 @@ void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long lon
     d.height = v.height;
     d.filter = filter == STF_FILTER_PER_VIEW ? v.filter : filter;
     int tw = v.tile_w, th = v.tile_h;
-    if (tw == 0 || mode == STF_MODE_FULL || mode == STF_MODE_ONE_TAP) { tw = 8; th = 4; }
+    if (tw == 0 || (mode & kModeBase) <= STF_MODE_ONE_TAP) { tw = 8; th = 4; }
     d.tile_w = tw;
     d.tile_h = th;
     d.tiles_x = (v.width + tw - 1) / tw;
@@ -397,6 +397,7 @@ void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long lon
     d.neural = t->decoder_params;
     stf_device_state(&d.flags, nullptr);
     d.affine = (v.H[6] == 0.0f && v.H[7] == 0.0f && v.H[8] == 1.0f) ? 1 : 0;
+    d.estimator = ((mode >> STF_MODE_EST_SHIFT) & 7) | ((mode & STF_MODE_FLAG_CLAMP) ? 8 : 0);
     if (!v.shading) d.shade_layout = 0;
     else if (v.ch_albedo == 0 && v.ch_normal == 3 && v.ch_rough == 5 && v.ch_ao == 6) d.shade_layout = 1;
     else if (v.ch_albedo == 0 && v.ch_normal == 4 && v.ch_rough == -1 && v.ch_ao == -1) d.shade_layout = 2;
@@ -432,10 +433,31 @@ cudaError_t stf_launch_single(const DevView& d, int kind, int mode, cudaStream_t
 // sharing mode.
 stf_status stf_check_mode(int mode)
 {
-    const int base = mode & ~STF_MODE_FLAG_EXACT;
-    if (base < STF_MODE_FULL || base > STF_MODE_WAVE4) return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d", mode);
+    const int base = mode & kModeBase;
+    const int est = (mode >> STF_MODE_EST_SHIFT) & 7;
+    const int known = kModeBase | STF_MODE_FLAG_EXACT | (7 << STF_MODE_EST_SHIFT) | STF_MODE_FLAG_CLAMP;
+    if (base > STF_MODE_WAVE4 || (mode & ~known) || est > STF_EST_REGRESSION)
+        return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d", mode);
     if ((mode & STF_MODE_FLAG_EXACT) && base < STF_MODE_QUAD2)
         return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: exact filtering needs a sharing mode", mode);
+    if ((est || (mode & STF_MODE_FLAG_CLAMP)) && base < STF_MODE_QUAD2)
+        return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: an estimator needs a sharing mode", mode);
+    if ((mode & STF_MODE_FLAG_CLAMP) && est == STF_EST_WIS)
+        return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: the weighted estimator is bounded already (no clamp)", mode);
+    if ((mode & STF_MODE_FLAG_EXACT) && est != STF_EST_WIS)
+        return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: exact filtering goes with the weighted estimator", mode);
+    return STF_OK;
+}
+
+// Alternative estimators are evaluation modes: one view of a stored material kind, 8x4 tiles.
+static stf_status check_alt(const stf_view* views, int n, int mode)
+{
+    if (((mode >> STF_MODE_EST_SHIFT) & 7) == STF_EST_WIS) return STF_OK;
+    if (n != 1) return stf_fail(STF_ERR_INVALID_ARG, "alternative estimators render one view per call");
+    if (views[0].tex->kind == K_NEURAL)
+        return stf_fail(STF_ERR_INVALID_ARG, "alternative estimators: stored material kinds only");
+    if (views[0].tile_w != 0 && (views[0].tile_w != 8 || views[0].tile_h != 4))
+        return stf_fail(STF_ERR_INVALID_ARG, "alternative estimators: 8x4 tiles only");
     return STF_OK;
 }
 
@@ -449,6 +471,7 @@ extern "C" stf_status stf_render_views(const stf_view* views, int n, int filter,
         stf_status s = stf_validate_view(views[i], i, filter, reuse_mode);
         if (s != STF_OK) return s;
     }
+    if (check_alt(views, n, reuse_mode) != STF_OK) return STF_ERR_INVALID_ARG;
     const float* lut = nullptr;
     stf_status s = stf_device_state(nullptr, &lut);
     if (s != STF_OK) return s;

@@ -23,6 +23,9 @@ constexpr float kPi = 3.14159265f;
 constexpr int kMaxCh = 8;
 constexpr int kWarpsPerBlock = 8;  // warps (pixel tiles in flight) per render block
 constexpr int kModeFlagExact = 16;  // STF_MODE_FLAG_EXACT of the C interface
+constexpr int kModeEstShift = 8;     // STF_MODE_EST_SHIFT: (mode >> 8) & 7 = the estimator
+constexpr int kModeFlagClamp = 2048; // STF_MODE_FLAG_CLAMP
+constexpr int kModeBase = 15;        // the stf_reuse_mode bits
 constexpr int kBatchMaxViews = 224; // views per persistent launch (their constants sit in a constant bank)
 
 // Material kinds with a dedicated kernel. Anything else is widened to FP32 at creation.
@@ -66,6 +69,8 @@ struct DevView {
     int affine;               // H[6] == H[7] == 0 and H[8] == 1: hw == 1 exactly, no division needed
     const void* neural;       // decoder parameters for K_NEURAL
     int* flags;               // device error counters: [0] timed-out waits
+    int estimator;            // alternative estimator (kernels compiled with ALT): 1 IS, 2 MIS,
+                              // 3 pairwise MIS, 4 regression; + 8: clamp to the texels' range
 };
 
 // A run of tiles of one view for the persistent multi-view kernel. variant = filter * 3 + tile

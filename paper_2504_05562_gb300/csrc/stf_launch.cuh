@@ -37,7 +37,7 @@ static int device_sms()
     return n > 0 ? n : 1;
 }
 
-template <int KIND, int F, int MODE, int TW, int TH, bool EX = false>
+template <int KIND, int F, int MODE, int TW, int TH, bool EX = false, bool ALT = false>
 static cudaError_t launch_one(const DevView& v, cudaStream_t s)
 {
     const dim3 grid((unsigned)((v.tiles_x + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)v.tiles_y);
@@ -52,7 +52,7 @@ static cudaError_t launch_one(const DevView& v, cudaStream_t s)
         const unsigned blocks = (unsigned)(groups < (long long)per_sm * device_sms() ? groups : (long long)per_sm * device_sms());
         k_render_neural<F, MODE, TW, TH, EX><<<blocks, kNnPipeThreads, dyn, s>>>(v);
     } else {
-        k_render_view<KIND, F, MODE, TW, TH, EX><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
+        k_render_view<KIND, F, MODE, TW, TH, EX, ALT><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
     }
     return cudaGetLastError();
 }
@@ -66,10 +66,16 @@ static cudaError_t launch_tiles(const DevView& v, cudaStream_t s)
     return cudaErrorInvalidValue;
 }
 
-// Sharing modes; exact filtering exists for the bilinear filter (the B-spline ignores the flag).
+// Sharing modes; exact filtering exists for the bilinear filter (the B-spline ignores the flag);
+// the alternative estimators (v.estimator != 0) for stored kinds on 8x4 tiles.
 template <int KIND, int F, int MODE>
 static cudaError_t launch_sharing(const DevView& v, bool ex, cudaStream_t s)
 {
+    if constexpr (KIND != K_NEURAL)
+        if (v.estimator != 0) {
+            if (v.tile_w != 8 || v.tile_h != 4) return cudaErrorInvalidValue;
+            return launch_one<KIND, F, MODE, 8, 4, false, true>(v, s);
+        }
     if constexpr (F == 0)
         if (ex) return launch_tiles<KIND, F, MODE, true>(v, s);
     return launch_tiles<KIND, F, MODE, false>(v, s);
@@ -79,7 +85,7 @@ template <int KIND, int F>
 static cudaError_t launch_modes(const DevView& v, int mode, cudaStream_t s)
 {
     const bool ex = (mode & kModeFlagExact) != 0;
-    switch (mode & ~kModeFlagExact) {
+    switch (mode & kModeBase) {
     case 0: return launch_one<KIND, F, 0, 8, 4>(v, s);  // no sharing: tile shape irrelevant
     case 1: return launch_one<KIND, F, 1, 8, 4>(v, s);
     case 2: return launch_sharing<KIND, F, 2>(v, ex, s);
@@ -235,7 +241,7 @@ template <int KIND>
 cudaError_t launch_batch_kind(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant,
                               int* per_sm, cudaStream_t s)
 {
-    switch (mode & ~kModeFlagExact) {  // the flag is in the variant
+    switch (mode & kModeBase) {  // the exact flag is in the variant
     case 0: return launch_batch_mode<KIND, 0>(items, n_items, counter, grid, variant, per_sm, s);
     case 1: return launch_batch_mode<KIND, 1>(items, n_items, counter, grid, variant, per_sm, s);
     case 2: return launch_batch_mode<KIND, 2>(items, n_items, counter, grid, variant, per_sm, s);

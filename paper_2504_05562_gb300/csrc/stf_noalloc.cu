@@ -125,6 +125,8 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
     if (filter != STF_FILTER_BILINEAR && filter != STF_FILTER_BSPLINE3 && filter != STF_FILTER_PER_VIEW)
         return stf_fail(STF_ERR_INVALID_ARG, "filter %d", filter);
     if (stf_check_mode(reuse_mode) != STF_OK) return STF_ERR_INVALID_ARG;
+    if ((reuse_mode >> STF_MODE_EST_SHIFT) & 7)
+        return stf_fail(STF_ERR_INVALID_ARG, "stf_render_views_noalloc: the weighted estimator only");
     for (int i = 0; i < n; ++i) {
         stf_status s = stf_validate_view(views[i], i, filter, reuse_mode);
         if (s != STF_OK) return s;

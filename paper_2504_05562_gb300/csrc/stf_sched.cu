@@ -116,7 +116,7 @@ void resolve(const stf_view& v, int filter, int mode, int* tw, int* th, int* sch
     if (v.tile_w) { *tw = v.tile_w; *th = v.tile_h; }
     else if (it != g_tune.end()) { *tw = it->second.tile_w; *th = it->second.tile_h; }
     else { *tw = 8; *th = 4; }
-    if (mode == STF_MODE_FULL || mode == STF_MODE_ONE_TAP) { *tw = 8; *th = 4; }
+    if ((mode & kModeBase) <= STF_MODE_ONE_TAP || ((mode >> STF_MODE_EST_SHIFT) & 7)) { *tw = 8; *th = 4; }
 }
 
 int tile_code(int tw, int th) { return tw == 8 ? 0 : (tw == 4 ? 1 : 2); }
@@ -380,7 +380,7 @@ void stf_resolve_view_config_nohalloc(const stf_view& v, int filter, int mode, i
     if (v.tile_w) { *tw = v.tile_w; *th = v.tile_h; }
     else if (it != g_tune.end()) { *tw = it->second.tile_w; *th = it->second.tile_h; }
     else { *tw = 8; *th = 4; }
-    if (mode == STF_MODE_FULL || mode == STF_MODE_ONE_TAP) { *tw = 8; *th = 4; }
+    if ((mode & kModeBase) <= STF_MODE_ONE_TAP || ((mode >> STF_MODE_EST_SHIFT) & 7)) { *tw = 8; *th = 4; }
 }
 
 stf_status stf_render_batch(const stf_view* views, int n, int filter, int mode, unsigned long long seed)
@@ -424,6 +424,8 @@ extern "C" stf_status stf_autotune(const stf_view* views, int n, int filter, int
 {
     if (!views || n < 1) return stf_fail(STF_ERR_INVALID_ARG, "stf_autotune: need n >= 1 views");
     if (stf_check_mode(reuse_mode) != STF_OK) return STF_ERR_INVALID_ARG;
+    if ((reuse_mode >> STF_MODE_EST_SHIFT) & 7)
+        return stf_fail(STF_ERR_INVALID_ARG, "stf_autotune: the weighted estimator only");
     for (int i = 0; i < n; ++i) {
         stf_status s = stf_validate_view(views[i], i, filter, reuse_mode);
         if (s != STF_OK) return s;
@@ -441,7 +443,7 @@ extern "C" stf_status stf_autotune(const stf_view* views, int n, int filter, int
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const bool shares = reuse_mode >= STF_MODE_QUAD2;
+    const bool shares = (reuse_mode & kModeBase) >= STF_MODE_QUAD2;
     stf_status st = STF_OK;
     for (const auto& kv : rep) {
         TuneEntry best{8, 4, kDefaultSchedule, 1e30f};

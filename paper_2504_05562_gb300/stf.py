@@ -17,6 +17,9 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, 
 FILTER_BILINEAR, FILTER_BSPLINE3, FILTER_PER_VIEW = 0, 1, -1
 MODE_FULL, MODE_ONE_TAP, MODE_QUAD2, MODE_WAVE2, MODE_WAVE3, MODE_WAVE4 = range(6)
 MODE_FLAG_EXACT = 16  # exact filtering (bilinear), OR'd into a sharing mode
+# alternative estimators (evaluation modes): mode | (EST_* << MODE_EST_SHIFT) [| MODE_FLAG_CLAMP]
+MODE_EST_SHIFT, MODE_FLAG_CLAMP = 8, 2048
+EST_WIS, EST_IS, EST_MIS, EST_PAIRWISE_MIS, EST_REGRESSION = range(5)
 FMT_FP32, FMT_FP16, FMT_BF16, FMT_E4M3, FMT_UNORM8, FMT_NEURAL = range(6)
 MODE_NAMES = {"full": 0, "one_tap": 1, "quad2": 2, "wave2": 3, "wave3": 4, "wave4": 5}
 
@@ -212,6 +215,7 @@ def make_view(view: dict, tex: Texture, out, debug_indices=None, debug_channels=
     v.frame = int(view.get("frame", 0))
     v.view_id = int(view.get("view_id", 0))
     v.tex = tex.handle
+    v._keep = (tex, out, debug_indices, debug_channels)  # the view holds what its pointers name
     v.out_rgba = out.data_ptr()
     v.out_pitch_floats = int(out.stride(0)) if out.dim() == 3 else 0
     v.debug_indices = debug_indices.data_ptr() if debug_indices is not None else None
