@@ -32,6 +32,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms/4K frame & Gpix/s: reuse-STF vs 1-sample STF vs full filter; PSNR dB"
 MODES = {"full": 0, "one_tap": 1, "quad2": 2, "wave2": 3, "wave3": 4, "wave4": 5}
+# exact filtering (bilinear only): the sharing modes | STF_MODE_FLAG_EXACT
+EXACT_MODES = {"quad2_exact": 2 | 16, "wave2_exact": 3 | 16, "wave3_exact": 4 | 16, "wave4_exact": 5 | 16}
 FMTS = {"fp32": 0, "fp16": 1, "bf16": 2, "e4m3": 3}
 REC_BYTES = {"fp32": 32, "fp16": 16, "bf16": 16, "e4m3": 8}
 
@@ -357,7 +359,8 @@ def run_ours(a):
     if not a.no_extras and rank == 0:
         extras = {}
         refs = {}
-        for name, m in MODES.items():
+        modes = dict(MODES, **(EXACT_MODES if a.filter == "bilinear" else {}))
+        for name, m in modes.items():
             tt = time_mode(stf, torch, tex, view, m, max(5, a.steps // 2), 3, flush, rank, out)
             med = statistics.median(tt)
             extras[name] = {"ms_median": med, "gpix_s": a.width * a.height / (med * 1e-3) / 1e9}
@@ -365,10 +368,12 @@ def run_ours(a):
             stf.render_views([stf.make_view(dict(view, frame=0), tex, img)], stf.FILTER_PER_VIEW, m, 0)
             refs[name] = img
         torch.cuda.synchronize()
-        for name in MODES:
+        for name in modes:
             extras[name]["psnr_db_vs_full"] = psnr(torch, refs[name], refs["full"]) if name != "full" else None
         line["modes"] = extras
         line["reuse_time_over_one_tap"] = extras[a.mode]["ms_median"] / extras["one_tap"]["ms_median"]
+        if a.workload == "c3":
+            line["estimators"] = estimators_extra(a, stf, torch, tex, view, flush, rank, out, refs["full"])
         line["e2e"] = e2e(a, stf, torch, mat, view)
         if not a.no_neural:
             line["neural"] = neural_extra(a, stf, torch, W, view, flush)
@@ -382,6 +387,24 @@ def run_ours(a):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def estimators_extra(a, stf, torch, tex, view, flush, rank, out, full):
+    """The estimator comparison of Section 5.2 on the benchmark frame (the reuse mode, 8x4 tiles):
+    time and PSNR against the full filter of each alternative estimator, plain and clamped."""
+    res = {}
+    v = dict(view, tile=(8, 4))
+    names = {"is": stf.EST_IS, "mis": stf.EST_MIS, "pairwise_mis": stf.EST_PAIRWISE_MIS, "regression": stf.EST_REGRESSION}
+    for name, est in names.items():
+        for clamp in (False, True):
+            m = MODES[a.mode] | (est << stf.MODE_EST_SHIFT) | (stf.MODE_FLAG_CLAMP if clamp else 0)
+            tt = time_mode(stf, torch, tex, v, m, 5, 2, flush, rank, out)
+            img = torch.empty_like(out)
+            stf.render_views([stf.make_view(dict(v, frame=0), tex, img)], stf.FILTER_PER_VIEW, m, 0)
+            torch.cuda.synchronize()
+            res[name + ("_clamped" if clamp else "")] = {"ms_median": statistics.median(tt),
+                                                         "psnr_db_vs_full": psnr(torch, img, full)}
+    return res
 
 
 def time_fn(torch, fn, steps, warmup, flush):
