@@ -55,7 +55,10 @@ typedef enum { STF_FILTER_BILINEAR = 0, STF_FILTER_BSPLINE3 = 1, STF_FILTER_PER_
  *            min(k,2) rows by round(k*k/2) columns. */
 typedef enum {
     STF_MODE_FULL = 0, STF_MODE_ONE_TAP = 1, STF_MODE_QUAD2 = 2,
-    STF_MODE_WAVE2 = 3, STF_MODE_WAVE3 = 4, STF_MODE_WAVE4 = 5
+    STF_MODE_WAVE2 = 3, STF_MODE_WAVE3 = 4, STF_MODE_WAVE4 = 5,
+    STF_MODE_SPARSE9 = 6  /* pseudorandom sparse 9-lane footprints, the patterns set by
+                           * stf_set_sparse_footprints, pattern frame % patterns (Section
+                           * "Sharing Footprints Within Waves"); views take the patterns' tile */
 } stf_reuse_mode;
 
 /* Exact filtering (Section "Exact Filtering"), OR'd into a sharing mode (QUAD2 .. WAVE4): with
@@ -229,6 +232,29 @@ stf_status stf_autotune_clear(void);
 #define STF_NOALLOC_MAX_ITEMS 262144
 stf_status stf_render_views_noalloc(const stf_view* views, int n, int filter, int reuse_mode,
                                     unsigned long long seed);
+
+/* Pseudorandom sparse sharing footprints (Section "Sharing Footprints Within Waves"; Appendix
+ * "Pseudorandom Sparse Footprint Generation Algorithm"): for each of `patterns` patterns and each
+ * lane of a tile_w x tile_h tile (32 lanes), `count` lane indices (the lane first, then count - 1
+ * distinct others) into table[pattern][lane][count] (host). Three stages per restart: per lane
+ * `candidates` candidate sets drawn at normally distributed offsets (standard deviation `sigma`
+ * lanes per axis, relaxed near the tile's border), the best of `picks` random choices by the
+ * standard deviation of the lanes' usage counts, then coordinate descent over the candidates;
+ * the best of `restarts` restarts is kept, its score in scores[pattern] (host, may be NULL).
+ * Deterministic for a seed. The paper's setting: count 9, sigma 1.4, 16-32 candidates, 10,000
+ * picks, 30 restarts. Host only, synchronous. Errors: STF_ERR_INVALID_ARG. */
+#define STF_SPARSE_MAX_COUNT 16
+stf_status stf_sparse_footprints(int tile_w, int tile_h, int count, double sigma, int candidates, int picks,
+                                 int restarts, unsigned long long seed, int patterns, signed char* table,
+                                 double* scores);
+
+/* Sets the current device's footprint patterns for STF_MODE_SPARSE9: table[patterns][32][9]
+ * (host) of lane indices for a tile_w x tile_h tile, own lane first, distinct, 0..31 (as
+ * stf_sparse_footprints makes with count 9). Frame f uses pattern f % patterns. Waits for the
+ * device (the old patterns may be in use), may allocate device memory. Errors:
+ * STF_ERR_INVALID_ARG for a malformed table (nothing changes). */
+#define STF_SPARSE_MAX_PATTERNS 256
+stf_status stf_set_sparse_footprints(const signed char* table, int patterns, int tile_w, int tile_h);
 
 /* Frees a texture (NULL is a no-op). The caller ensures no enqueued work still reads it. */
 stf_status stf_destroy(stf_texture* tex);

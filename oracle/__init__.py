@@ -24,7 +24,7 @@ HDR = os.path.join(HERE, "stf_oracle.h")
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 BILINEAR, BSPLINE3 = 0, 1
-FULL, ONE_TAP, QUAD2, WAVE2, WAVE3, WAVE4 = 0, 1, 2, 3, 4, 5
+FULL, ONE_TAP, QUAD2, WAVE2, WAVE3, WAVE4, SPARSE9 = 0, 1, 2, 3, 4, 5, 6
 FLAG_EXACT = 16  # exact filtering (bilinear), OR'd into a sharing mode
 EST_SHIFT, FLAG_CLAMP = 8, 2048  # alternative estimators: mode | (est << EST_SHIFT) [| FLAG_CLAMP]
 EST_WIS, EST_IS, EST_MIS, EST_PMIS, EST_REG = range(5)
@@ -74,6 +74,7 @@ class RefView(C.Structure):
         ("shading", C.c_int), ("ch_albedo", C.c_int), ("ch_normal", C.c_int), ("ch_rough", C.c_int),
         ("ch_ao", C.c_int), ("roughness", C.c_float), ("filter", C.c_int),
         ("tile_w", C.c_int), ("tile_h", C.c_int), ("frame", C.c_int), ("view_id", C.c_int),
+        ("fp_table", C.c_void_p), ("fp_patterns", C.c_int),
     ]
 
 
@@ -308,6 +309,12 @@ def _view_struct(view):
     v.tile_w, v.tile_h = view.get("tile", (8, 4))
     v.frame = int(view.get("frame", 0))
     v.view_id = int(view.get("view_id", 0))
+    fp = view.get("footprints")  # int8 [patterns, 32, 9] for SPARSE9
+    if fp is not None:
+        fp = np.ascontiguousarray(fp, np.int8)
+        v._fp = fp  # kept alive with the struct
+        v.fp_table = fp.ctypes.data
+        v.fp_patterns = fp.shape[0]
     return v
 
 

@@ -495,6 +495,19 @@ static int full_filter(const ref_material* m, int f, int C, float cx, float cy, 
     return 1;
 }
 
+/* The footprint of a lane: the square footprints of the sharing modes, or the lane's row of the
+ * view's sparse pattern for this frame. */
+static int lane_footprint(const job_t* J, int lane, int* list)
+{
+    const ref_view* v = J->v;
+    if (J->mode == REF_SPARSE9) {
+        const signed char* row = v->fp_table + ((size_t)(v->frame % v->fp_patterns) * 32 + lane) * 9;
+        for (int i = 0; i < 9; ++i) list[i] = row[i];
+        return 9;
+    }
+    return stf_ref_footprint(J->mode, v->tile_w, v->tile_h, lane, list);
+}
+
 /* Lane j's filter weight (its PMF) at texel (nx, ny). */
 static float pmf_at(int f, const float* cx, const float* cy, int j, int nx, int ny)
 {
@@ -619,13 +632,13 @@ static void render_tile(const job_t* J, int tx, int ty)
             full_filter(m, f, C, cx[lane], cy[lane], NULL, NULL, NULL, 0, res);
         } else if (J->est != REF_EST_WIS) {
             int list[16];
-            int n = stf_ref_footprint(J->mode, tw, th, lane, list);
+            int n = lane_footprint(J, lane, list);
             alt_estimate(J->est, J->clamp, f, C, lane, cx, cy, ix, iy, p, (const float(*)[REF_MAX_CH])T, list, n, res);
         } else {
             /* weighted importance sampling over the footprint (Section 4.5):
              * w_j = p_c(x_j) / p_j(x_j), result = sum w_j T_j / sum w_j */
             int list[16];
-            int n = stf_ref_footprint(J->mode, tw, th, lane, list);
+            int n = lane_footprint(J, lane, list);
             float acc[REF_MAX_CH] = {0};
             float wsum = 0.0f;
             for (int i = 0; i < n; ++i) {
@@ -713,7 +726,12 @@ int stf_ref_render(const ref_material* m, const ref_view* v, int mode, uint64_t 
     const int est = (mode >> REF_EST_SHIFT) & 7;
     const int clamp = (mode & REF_FLAG_CLAMP) != 0;
     mode &= 15;
-    if (mode < REF_FULL || mode > REF_WAVE4) return 1;
+    if (mode < REF_FULL || mode > REF_SPARSE9) return 1;
+    if (mode == REF_SPARSE9) {
+        if (!v->fp_table || v->fp_patterns < 1) return 1;
+        for (long i = 0; i < (long)v->fp_patterns * 32 * 9; ++i)
+            if (v->fp_table[i] < 0 || v->fp_table[i] > 31) return 1;
+    }
     if (exact && mode < REF_QUAD2) return 1; /* exact filtering needs shared samples */
     if ((est != REF_EST_WIS || clamp) && mode < REF_QUAD2) return 1;
     if (est > REF_EST_REG || (clamp && est == REF_EST_WIS) || (exact && est != REF_EST_WIS)) return 1;

@@ -26,7 +26,9 @@ extern "C" {
 enum { REF_BILINEAR = 0, REF_BSPLINE3 = 1 };
 
 /* Sharing modes (Sections 4.3.1, 4.5; Table 1). FULL is the deterministic filter. */
-enum { REF_FULL = 0, REF_ONE_TAP = 1, REF_QUAD2 = 2, REF_WAVE2 = 3, REF_WAVE3 = 4, REF_WAVE4 = 5 };
+enum { REF_FULL = 0, REF_ONE_TAP = 1, REF_QUAD2 = 2, REF_WAVE2 = 3, REF_WAVE3 = 4, REF_WAVE4 = 5,
+       REF_SPARSE9 = 6 /* the view's footprint table, pattern frame % patterns (Section
+                        * "Sharing Footprints Within Waves") */ };
 
 /* Exact filtering (Section "Exact Filtering"), OR'd into a sharing mode: with the bilinear filter,
  * a pixel whose footprint samples include every texel of positive weight in its own filter
@@ -90,6 +92,9 @@ typedef struct {
     int filter;
     int tile_w, tile_h;            /* warp pixel tile, tile_w * tile_h == 32 */
     int frame, view_id;
+    /* REF_SPARSE9: fp_table[fp_patterns][32][9] lane indices (own lane first), else NULL */
+    const signed char* fp_table;
+    int fp_patterns;
 } ref_view;
 
 /* Counter-based hash (pcg4d, Jarzynski and Olano 2020), in place. */

@@ -77,12 +77,72 @@ cudaError_t stf_resident_blocks(const void* kernel, int threads, int dyn_bytes, 
 
 // ------------------------------------------------------------------------------ per-device state
 
+static bool tile_ok(int tw, int th);
+
 struct DeviceState {
     bool ready = false;
     float* unorm_lut = nullptr;  // q / 255 for q = 0..255, computed on the host in IEEE FP32
     int* flags = nullptr;        // [0] timeout, [1] device assert
+    uint8_t* fp = nullptr;       // sparse footprint patterns [fp_patterns][32][16] (STF_MODE_SPARSE9)
+    int fp_patterns = 0, fp_capacity = 0, fp_tw = 0, fp_th = 0;
 };
 static DeviceState g_dev[64];
+
+static DeviceState* current_state()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    return &g_dev[dev];
+}
+
+// The current device's sparse footprints: false if none were set.
+bool stf_sparse_state(const uint8_t** table, int* patterns, int* tile_w, int* tile_h)
+{
+    const DeviceState* d = current_state();
+    if (!d || !d->fp || d->fp_patterns < 1) return false;
+    if (table) *table = d->fp;
+    if (patterns) *patterns = d->fp_patterns;
+    if (tile_w) *tile_w = d->fp_tw;
+    if (tile_h) *tile_h = d->fp_th;
+    return true;
+}
+
+extern "C" stf_status stf_set_sparse_footprints(const signed char* table, int patterns, int tile_w, int tile_h)
+{
+    if (!table || patterns < 1 || patterns > STF_SPARSE_MAX_PATTERNS || !tile_ok(tile_w, tile_h))
+        return stf_fail(STF_ERR_INVALID_ARG, "stf_set_sparse_footprints: bad arguments");
+    std::vector<uint8_t> h((size_t)patterns * 32 * 16, 0);
+    for (int p = 0; p < patterns; ++p)
+        for (int l = 0; l < 32; ++l) {
+            const signed char* row = table + ((size_t)p * 32 + l) * 9;
+            if (row[0] != l) return stf_fail(STF_ERR_INVALID_ARG, "pattern %d lane %d: the own lane must come first", p, l);
+            for (int i = 0; i < 9; ++i) {
+                if (row[i] < 0 || row[i] > 31) return stf_fail(STF_ERR_INVALID_ARG, "pattern %d lane %d: lane index %d", p, l, row[i]);
+                for (int k = 0; k < i; ++k)
+                    if (row[k] == row[i]) return stf_fail(STF_ERR_INVALID_ARG, "pattern %d lane %d: repeated lane %d", p, l, row[i]);
+                h[((size_t)p * 32 + l) * 16 + i] = (uint8_t)row[i];
+            }
+        }
+    stf_status st = stf_device_state(nullptr, nullptr);
+    if (st != STF_OK) return st;
+    DeviceState& d = *current_state();
+    cudaError_t e;
+    if (patterns > d.fp_capacity) {
+        if (d.fp && (e = cudaFree(d.fp)) != cudaSuccess) return stf_cuda_fail(e, "cudaFree(footprints)");
+        d.fp = nullptr;
+        d.fp_patterns = d.fp_capacity = 0;
+        if ((e = cudaMalloc(&d.fp, h.size())) != cudaSuccess) return stf_cuda_fail(e, "cudaMalloc(footprints)");
+        d.fp_capacity = patterns;
+    }
+    // synchronous: the previous patterns may still be read by enqueued work
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return stf_cuda_fail(e, "synchronize");
+    if ((e = cudaMemcpy(d.fp, h.data(), h.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return stf_cuda_fail(e, "cudaMemcpy(footprints)");
+    d.fp_patterns = patterns;
+    d.fp_tw = tile_w;
+    d.fp_th = tile_h;
+    return STF_OK;
+}
 
 stf_status stf_device_state(int** flags, const float** lut)
 {
@@ -353,7 +413,14 @@ stf_status stf_validate_view(const stf_view& v, int i, int filter, int mode)
     }
     for (int k = 0; k < 9; ++k)
         if (!std::isfinite(v.H[k])) return stf_fail(STF_ERR_INVALID_ARG, "view %d: H[%d] not finite", i, k);
-    (void)mode;
+    if ((mode & kModeBase) == STF_MODE_SPARSE9) {
+        int tw = 0, th = 0;
+        if (!stf_sparse_state(nullptr, nullptr, &tw, &th))
+            return stf_fail(STF_ERR_INVALID_ARG, "view %d: STF_MODE_SPARSE9 without stf_set_sparse_footprints", i);
+        if (v.tile_w != 0 && (v.tile_w != tw || v.tile_h != th))
+            return stf_fail(STF_ERR_INVALID_ARG, "view %d: tile %dx%d differs from the sparse footprints' %dx%d", i,
+                            v.tile_w, v.tile_h, tw, th);
+    }
     return STF_OK;
 }
 
@@ -369,6 +436,12 @@ void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long lon
     d.filter = filter == STF_FILTER_PER_VIEW ? v.filter : filter;
     int tw = v.tile_w, th = v.tile_h;
     if (tw == 0 || (mode & kModeBase) <= STF_MODE_ONE_TAP) { tw = 8; th = 4; }
+    if ((mode & kModeBase) == STF_MODE_SPARSE9) {  // the frame's pattern, on the patterns' tile
+        const uint8_t* fp = nullptr;
+        int np = 1;
+        stf_sparse_state(&fp, &np, &tw, &th);
+        d.fp = fp ? fp + (size_t)(v.frame % np) * 32 * 16 : nullptr;
+    }
     d.tile_w = tw;
     d.tile_h = th;
     d.tiles_x = (v.width + tw - 1) / tw;
@@ -436,7 +509,7 @@ stf_status stf_check_mode(int mode)
     const int base = mode & kModeBase;
     const int est = (mode >> STF_MODE_EST_SHIFT) & 7;
     const int known = kModeBase | STF_MODE_FLAG_EXACT | (7 << STF_MODE_EST_SHIFT) | STF_MODE_FLAG_CLAMP;
-    if (base > STF_MODE_WAVE4 || (mode & ~known) || est > STF_EST_REGRESSION)
+    if (base > STF_MODE_SPARSE9 || (mode & ~known) || est > STF_EST_REGRESSION)
         return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d", mode);
     if ((mode & STF_MODE_FLAG_EXACT) && base < STF_MODE_QUAD2)
         return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: exact filtering needs a sharing mode", mode);
@@ -454,6 +527,8 @@ static stf_status check_alt(const stf_view* views, int n, int mode)
 {
     if (((mode >> STF_MODE_EST_SHIFT) & 7) == STF_EST_WIS) return STF_OK;
     if (n != 1) return stf_fail(STF_ERR_INVALID_ARG, "alternative estimators render one view per call");
+    if ((mode & kModeBase) == STF_MODE_SPARSE9)
+        return stf_fail(STF_ERR_INVALID_ARG, "alternative estimators: square footprints only");
     if (views[0].tex->kind == K_NEURAL)
         return stf_fail(STF_ERR_INVALID_ARG, "alternative estimators: stored material kinds only");
     if (views[0].tile_w != 0 && (views[0].tile_w != 8 || views[0].tile_h != 4))

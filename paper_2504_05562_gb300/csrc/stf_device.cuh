@@ -26,6 +26,7 @@ constexpr int kModeFlagExact = 16;  // STF_MODE_FLAG_EXACT of the C interface
 constexpr int kModeEstShift = 8;     // STF_MODE_EST_SHIFT: (mode >> 8) & 7 = the estimator
 constexpr int kModeFlagClamp = 2048; // STF_MODE_FLAG_CLAMP
 constexpr int kModeBase = 15;        // the stf_reuse_mode bits
+constexpr int kModeSparse9 = 6;      // STF_MODE_SPARSE9: 9-element pseudorandom sparse footprints
 constexpr int kBatchMaxViews = 224; // views per persistent launch (their constants sit in a constant bank)
 
 // Material kinds with a dedicated kernel. Anything else is widened to FP32 at creation.
@@ -69,6 +70,7 @@ struct DevView {
     int affine;               // H[6] == H[7] == 0 and H[8] == 1: hw == 1 exactly, no division needed
     const void* neural;       // decoder parameters for K_NEURAL
     int* flags;               // device error counters: [0] timed-out waits
+    const uint8_t* fp;        // STF_MODE_SPARSE9: the frame's pattern, [32 lanes][16] lane indices
     int estimator;            // alternative estimator (kernels compiled with ALT): 1 IS, 2 MIS,
                               // 3 pairwise MIS, 4 regression; + 8: clamp to the texels' range
 };
@@ -407,6 +409,12 @@ template <int C> __device__ __forceinline__ float4 finish_pixel(const DevView& v
 // Source-lane block of the sharing footprint (row-major kx x ky block at (ox, oy)); the same
 // placement rule as the oracle: QUAD2 = aligned 2x2; WAVEk = ky = min(k, TH) rows,
 // kx = min(TW, round(k^2 / ky)) columns, centred on the lane and shifted inside the tile.
+template <int MODE, int TW, int TH> struct Footprint;
+// Pseudorandom sparse footprints: 9 lanes per lane from a table (the shape constants are nominal).
+template <int TW, int TH> struct Footprint<6, TW, TH> {
+    static constexpr int KX = 9, KY = 1, N = 9;
+    __device__ static __forceinline__ int base(int, int) { return 0; }
+};
 template <int MODE, int TW, int TH> struct Footprint {
     static constexpr int k = MODE == 3 ? 2 : (MODE == 4 ? 3 : (MODE == 5 ? 4 : 2));
     static constexpr int KY = MODE == 2 ? 2 : (k < TH ? k : TH);

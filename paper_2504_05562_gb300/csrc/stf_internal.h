@@ -36,6 +36,9 @@ void stf_resolve_view_config_nohalloc(const stf_view& v, int filter, int mode, i
 // STF_OK for a valid reuse mode (optionally with STF_MODE_FLAG_EXACT), else sets the error.
 stf_status stf_check_mode(int mode);
 
+// The current device's sparse footprint patterns (stf_set_sparse_footprints); false if none.
+bool stf_sparse_state(const uint8_t** table, int* patterns, int* tile_w, int* tile_h);
+
 // resident blocks per SM, counted from the kernel's resources (stf_api.cu)
 cudaError_t stf_resident_blocks(const void* kernel, int threads, int dyn_bytes, int* n);
 

@@ -243,61 +243,68 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
             if constexpr (ALT) {
                 alt_combine<C, F, FP, TW, RPL>(v.estimator, lane, cx, cy, b0, rec, res);
             } else {
-                const int b0 = FP::base(lx, ly);
                 float2 acc[C / 2];
-    #pragma unroll
+#pragma unroll
                 for (int c = 0; c < C / 2; ++c) acc[c] = make_float2(0.0f, 0.0f);
                 float wsum = 0.0f;
                 uint32_t srcs = 0;  // exact filtering: per bilinear tap, 1 + a lane holding its texel
-    #pragma unroll
-                for (int r = 0; r < FP::KY; ++r) {
-    #pragma unroll
-                    for (int q = 0; q < FP::KX; ++q) {
-                        const int src = b0 + r * TW + q;
-                        const float4 m = rec[RPL * src];
-                        float wx, wy;
-                        if constexpr (F == 0) {  // W(c - n) evaluated as the oracle does
-                            wx = w_bilinear(__fsub_rn(cx, m.x));
-                            wy = w_bilinear(__fsub_rn(cy, m.y));
-                            if constexpr (EX) {
-                                const uint32_t pj = __float_as_uint(m.w);
-                                const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
-                                if (((kx | ky) & ~1) == 0) {
-                                    const int sh = 8 * (2 * ky + kx);
-                                    srcs = (srcs & ~(0xffu << sh)) | ((uint32_t)(src + 1) << sh);
-                                }
-                            }
-                        } else {
-                            // the same values read from this lane's taps: lattice points outside the
-                            // taps have zero weight
+                // one footprint element: lane src's record
+                auto visit = [&](int src) {
+                    const float4 m = rec[RPL * src];
+                    float wx, wy;
+                    if constexpr (F == 0) {  // W(c - n) evaluated as the oracle does
+                        wx = w_bilinear(__fsub_rn(cx, m.x));
+                        wy = w_bilinear(__fsub_rn(cy, m.y));
+                        if constexpr (EX) {
                             const uint32_t pj = __float_as_uint(m.w);
                             const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
-                            const bool in = ((kx | ky) & ~3) == 0;
-                            wx = in ? wtab[kx * 32 + lane] : 0.0f;
-                            wy = in ? wtab[(4 + ky) * 32 + lane] : 0.0f;
+                            if (((kx | ky) & ~1) == 0) {
+                                const int sh = 8 * (2 * ky + kx);
+                                srcs = (srcs & ~(0xffu << sh)) | ((uint32_t)(src + 1) << sh);
+                            }
                         }
-                        const float wt = (src == lane) ? 1.0f : (wx * wy) * m.z;
-                        const float2 w2 = make_float2(wt, wt);
-                        const float4 t0 = rec[RPL * src + 1];
-                        acc[0] = __ffma2_rn(w2, make_float2(t0.x, t0.y), acc[0]);
-                        if constexpr (C > 2) acc[1 % (C / 2)] = __ffma2_rn(w2, make_float2(t0.z, t0.w), acc[1 % (C / 2)]);
-                        if constexpr (C > 4) {
-                            const float4 t1 = rec[RPL * src + 2];
-                            acc[2 % (C / 2)] = __ffma2_rn(w2, make_float2(t1.x, t1.y), acc[2 % (C / 2)]);
-                            acc[3 % (C / 2)] = __ffma2_rn(w2, make_float2(t1.z, t1.w), acc[3 % (C / 2)]);
-                        }
-                        wsum += wt;
+                    } else {
+                        // the same values read from this lane's taps: lattice points outside the
+                        // taps have zero weight
+                        const uint32_t pj = __float_as_uint(m.w);
+                        const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
+                        const bool in = ((kx | ky) & ~3) == 0;
+                        wx = in ? wtab[kx * 32 + lane] : 0.0f;
+                        wy = in ? wtab[(4 + ky) * 32 + lane] : 0.0f;
                     }
+                    const float wt = (src == lane) ? 1.0f : (wx * wy) * m.z;
+                    const float2 w2 = make_float2(wt, wt);
+                    const float4 t0 = rec[RPL * src + 1];
+                    acc[0] = __ffma2_rn(w2, make_float2(t0.x, t0.y), acc[0]);
+                    if constexpr (C > 2) acc[1 % (C / 2)] = __ffma2_rn(w2, make_float2(t0.z, t0.w), acc[1 % (C / 2)]);
+                    if constexpr (C > 4) {
+                        const float4 t1 = rec[RPL * src + 2];
+                        acc[2 % (C / 2)] = __ffma2_rn(w2, make_float2(t1.x, t1.y), acc[2 % (C / 2)]);
+                        acc[3 % (C / 2)] = __ffma2_rn(w2, make_float2(t1.z, t1.w), acc[3 % (C / 2)]);
+                    }
+                    wsum += wt;
+                };
+                if constexpr (MODE == kModeSparse9) {
+                    // the lane's row of the frame's sparse footprint pattern (own lane first)
+                    const uint4 row = __ldg(reinterpret_cast<const uint4*>(v.fp) + lane);
+                    const uint32_t w4[4] = {row.x, row.y, row.z, row.w};
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) visit((int)((w4[i >> 2] >> (8 * (i & 3))) & 0x1fu));
+                } else {
+#pragma unroll
+                    for (int r = 0; r < FP::KY; ++r)
+#pragma unroll
+                        for (int q = 0; q < FP::KX; ++q) visit(b0 + r * TW + q);
                 }
                 const float inv = rcp_approx(wsum);
-    #pragma unroll
+#pragma unroll
                 for (int c = 0; c < C / 2; ++c) { res[2 * c] = acc[c].x * inv; res[2 * c + 1] = acc[c].y * inv; }
                 if constexpr (EX && F == 0)
                     exact_bilinear<C>(ax, ay, srcs, res, [&](int j, float (&T)[C]) {
                         const float4 t0 = rec[RPL * j + 1];
                         const float4 t1 = C > 4 ? rec[RPL * j + 2] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                         const float tt[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-    #pragma unroll
+#pragma unroll
                         for (int c = 0; c < C; ++c) T[c] = tt[c];
                     });
             }

@@ -71,7 +71,7 @@ static cudaError_t launch_tiles(const DevView& v, cudaStream_t s)
 template <int KIND, int F, int MODE>
 static cudaError_t launch_sharing(const DevView& v, bool ex, cudaStream_t s)
 {
-    if constexpr (KIND != K_NEURAL)
+    if constexpr (KIND != K_NEURAL && MODE != kModeSparse9)
         if (v.estimator != 0) {
             if (v.tile_w != 8 || v.tile_h != 4) return cudaErrorInvalidValue;
             return launch_one<KIND, F, MODE, 8, 4, false, true>(v, s);
@@ -92,6 +92,7 @@ static cudaError_t launch_modes(const DevView& v, int mode, cudaStream_t s)
     case 3: return launch_sharing<KIND, F, 3>(v, ex, s);
     case 4: return launch_sharing<KIND, F, 4>(v, ex, s);
     case 5: return launch_sharing<KIND, F, 5>(v, ex, s);
+    case 6: return launch_sharing<KIND, F, 6>(v, ex, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -248,6 +249,7 @@ cudaError_t launch_batch_kind(const WorkItem* items, int n_items, int* counter, 
     case 3: return launch_batch_mode<KIND, 3>(items, n_items, counter, grid, variant, per_sm, s);
     case 4: return launch_batch_mode<KIND, 4>(items, n_items, counter, grid, variant, per_sm, s);
     case 5: return launch_batch_mode<KIND, 5>(items, n_items, counter, grid, variant, per_sm, s);
+    case 6: return launch_batch_mode<KIND, 6>(items, n_items, counter, grid, variant, per_sm, s);
     }
     return cudaErrorInvalidValue;
 }

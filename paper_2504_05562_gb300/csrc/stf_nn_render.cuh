@@ -141,41 +141,47 @@ struct NnRenderClient {
             for (int c = 0; c < 4; ++c) a2[c] = make_float2(0.0f, 0.0f);
             float wsum = 0.0f;
             uint32_t srcs = 0;  // exact filtering: per bilinear tap, 1 + a lane holding its texel
-#pragma unroll
-            for (int rr2 = 0; rr2 < FP::KY; ++rr2) {
-#pragma unroll
-                for (int q = 0; q < FP::KX; ++q) {
-                    const int src = b0 + rr2 * TW + q;
-                    const float4 m = sm.rec[slot][row0 + src];
-                    float wx, wy;
-                    if constexpr (F == 0) {
-                        wx = w_bilinear(__fsub_rn(cx, m.x));
-                        wy = w_bilinear(__fsub_rn(cy, m.y));
-                        if constexpr (EX) {
-                            const uint32_t pj = __float_as_uint(m.w);
-                            const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
-                            if (((kx | ky) & ~1) == 0) {
-                                const int sh = 8 * (2 * ky + kx);
-                                srcs = (srcs & ~(0xffu << sh)) | ((uint32_t)(src + 1) << sh);
-                            }
-                        }
-                    } else {
+            auto visit = [&](int src) {
+                const float4 m = sm.rec[slot][row0 + src];
+                float wx, wy;
+                if constexpr (F == 0) {
+                    wx = w_bilinear(__fsub_rn(cx, m.x));
+                    wy = w_bilinear(__fsub_rn(cy, m.y));
+                    if constexpr (EX) {
                         const uint32_t pj = __float_as_uint(m.w);
                         const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
-                        const bool in = ((kx | ky) & ~3) == 0;
-                        wx = in ? wtab[kx * 32 + lane] : 0.0f;
-                        wy = in ? wtab[(4 + ky) * 32 + lane] : 0.0f;
+                        if (((kx | ky) & ~1) == 0) {
+                            const int sh = 8 * (2 * ky + kx);
+                            srcs = (srcs & ~(0xffu << sh)) | ((uint32_t)(src + 1) << sh);
+                        }
                     }
-                    const float wt = (src == lane) ? 1.0f : (wx * wy) * m.z;
-                    const float2 w2 = make_float2(wt, wt);
-                    const float4* o = reinterpret_cast<const float4*>(sm.io[slot] + (row0 + src) * 32);
-                    const float4 t0 = o[0], t1 = o[1];
-                    a2[0] = __ffma2_rn(w2, make_float2(t0.x, t0.y), a2[0]);
-                    a2[1] = __ffma2_rn(w2, make_float2(t0.z, t0.w), a2[1]);
-                    a2[2] = __ffma2_rn(w2, make_float2(t1.x, t1.y), a2[2]);
-                    a2[3] = __ffma2_rn(w2, make_float2(t1.z, t1.w), a2[3]);
-                    wsum += wt;
+                } else {
+                    const uint32_t pj = __float_as_uint(m.w);
+                    const int kx = unpack_x(pj) - ax.base, ky = unpack_y(pj) - ay.base;
+                    const bool in = ((kx | ky) & ~3) == 0;
+                    wx = in ? wtab[kx * 32 + lane] : 0.0f;
+                    wy = in ? wtab[(4 + ky) * 32 + lane] : 0.0f;
                 }
+                const float wt = (src == lane) ? 1.0f : (wx * wy) * m.z;
+                const float2 w2 = make_float2(wt, wt);
+                const float4* o = reinterpret_cast<const float4*>(sm.io[slot] + (row0 + src) * 32);
+                const float4 t0 = o[0], t1 = o[1];
+                a2[0] = __ffma2_rn(w2, make_float2(t0.x, t0.y), a2[0]);
+                a2[1] = __ffma2_rn(w2, make_float2(t0.z, t0.w), a2[1]);
+                a2[2] = __ffma2_rn(w2, make_float2(t1.x, t1.y), a2[2]);
+                a2[3] = __ffma2_rn(w2, make_float2(t1.z, t1.w), a2[3]);
+                wsum += wt;
+            };
+            if constexpr (MODE == kModeSparse9) {
+                const uint4 fr = __ldg(reinterpret_cast<const uint4*>(v.fp) + lane);
+                const uint32_t w4[4] = {fr.x, fr.y, fr.z, fr.w};
+#pragma unroll
+                for (int i = 0; i < 9; ++i) visit((int)((w4[i >> 2] >> (8 * (i & 3))) & 0x1fu));
+            } else {
+#pragma unroll
+                for (int rr2 = 0; rr2 < FP::KY; ++rr2)
+#pragma unroll
+                    for (int q = 0; q < FP::KX; ++q) visit(b0 + rr2 * TW + q);
             }
             if constexpr (F == 1) __syncwarp();  // the table is rewritten by the warp's next round
             const float inv = rcp_approx(wsum);

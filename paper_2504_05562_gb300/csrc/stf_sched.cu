@@ -117,6 +117,7 @@ void resolve(const stf_view& v, int filter, int mode, int* tw, int* th, int* sch
     else if (it != g_tune.end()) { *tw = it->second.tile_w; *th = it->second.tile_h; }
     else { *tw = 8; *th = 4; }
     if ((mode & kModeBase) <= STF_MODE_ONE_TAP || ((mode >> STF_MODE_EST_SHIFT) & 7)) { *tw = 8; *th = 4; }
+    if ((mode & kModeBase) == STF_MODE_SPARSE9) stf_sparse_state(nullptr, nullptr, tw, th);
 }
 
 int tile_code(int tw, int th) { return tw == 8 ? 0 : (tw == 4 ? 1 : 2); }
@@ -381,6 +382,7 @@ void stf_resolve_view_config_nohalloc(const stf_view& v, int filter, int mode, i
     else if (it != g_tune.end()) { *tw = it->second.tile_w; *th = it->second.tile_h; }
     else { *tw = 8; *th = 4; }
     if ((mode & kModeBase) <= STF_MODE_ONE_TAP || ((mode >> STF_MODE_EST_SHIFT) & 7)) { *tw = 8; *th = 4; }
+    if ((mode & kModeBase) == STF_MODE_SPARSE9) stf_sparse_state(nullptr, nullptr, tw, th);
 }
 
 stf_status stf_render_batch(const stf_view* views, int n, int filter, int mode, unsigned long long seed)

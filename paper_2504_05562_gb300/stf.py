@@ -15,13 +15,13 @@ from . import build as _build
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_ASSERT = range(7)
 FILTER_BILINEAR, FILTER_BSPLINE3, FILTER_PER_VIEW = 0, 1, -1
-MODE_FULL, MODE_ONE_TAP, MODE_QUAD2, MODE_WAVE2, MODE_WAVE3, MODE_WAVE4 = range(6)
+MODE_FULL, MODE_ONE_TAP, MODE_QUAD2, MODE_WAVE2, MODE_WAVE3, MODE_WAVE4, MODE_SPARSE9 = range(7)
 MODE_FLAG_EXACT = 16  # exact filtering (bilinear), OR'd into a sharing mode
 # alternative estimators (evaluation modes): mode | (EST_* << MODE_EST_SHIFT) [| MODE_FLAG_CLAMP]
 MODE_EST_SHIFT, MODE_FLAG_CLAMP = 8, 2048
 EST_WIS, EST_IS, EST_MIS, EST_PAIRWISE_MIS, EST_REGRESSION = range(5)
 FMT_FP32, FMT_FP16, FMT_BF16, FMT_E4M3, FMT_UNORM8, FMT_NEURAL = range(6)
-MODE_NAMES = {"full": 0, "one_tap": 1, "quad2": 2, "wave2": 3, "wave3": 4, "wave4": 5}
+MODE_NAMES = {"full": 0, "one_tap": 1, "quad2": 2, "wave2": 3, "wave3": 4, "wave4": 5, "sparse9": 6}
 
 
 class StfError(RuntimeError):
@@ -57,7 +57,7 @@ EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_str
            "stf_decoder_get_params", "stf_decoder_set_params", "stf_decoder_decode", "stf_decoder_info",
            "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy", "stf_set_option", "stf_get_stat",
            "stf_autotune", "stf_view_config", "stf_autotune_save", "stf_autotune_load", "stf_autotune_clear",
-           "stf_render_views_noalloc")
+           "stf_render_views_noalloc", "stf_sparse_footprints", "stf_set_sparse_footprints")
 NOALLOC_MAX_VIEWS, NOALLOC_MAX_ITEMS = 224, 262144
 OPT_BATCH_GRAPHS = 1
 STAT_GRAPH_BUILDS, STAT_GRAPH_REPLAYS = 1, 2
@@ -100,6 +100,9 @@ def _bind_extra(L):
     L.stf_autotune_load.argtypes = [C.c_char_p]
     L.stf_autotune_clear.argtypes = []
     L.stf_render_views_noalloc.argtypes = [C.POINTER(View), C.c_int, C.c_int, C.c_int, C.c_ulonglong]
+    L.stf_set_sparse_footprints.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.stf_sparse_footprints.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
+                                        C.c_ulonglong, C.c_int, C.c_void_p, C.c_void_p]
     for n in ("stf_set_option", "stf_get_stat", "stf_autotune", "stf_view_config", "stf_autotune_save",
               "stf_autotune_load", "stf_autotune_clear", "stf_render_views_noalloc"):
         getattr(L, n).restype = C.c_int
@@ -281,3 +284,25 @@ def autotune_load(path):
 
 def autotune_clear():
     _check(load().stf_autotune_clear())
+
+
+# ----------------------------------------------------------------------------- sparse footprints
+
+def sparse_footprints(tile=(8, 4), count=9, sigma=1.4, candidates=32, picks=10000, restarts=30, seed=0, patterns=1):
+    """Pseudorandom sparse sharing footprints: int8 [patterns, 32, count] lane indices (own lane
+    first) and the per-pattern usage standard deviation (host code; no GPU needed)."""
+    import numpy as np
+    tab = np.zeros((patterns, 32, count), np.int8)
+    sc = np.zeros(patterns, np.float64)
+    _check(load().stf_sparse_footprints(int(tile[0]), int(tile[1]), int(count), float(sigma), int(candidates),
+                                        int(picks), int(restarts), int(seed) & (2 ** 64 - 1), int(patterns),
+                                        tab.ctypes.data, sc.ctypes.data))
+    return tab, sc
+
+
+def set_sparse_footprints(table, tile=(8, 4)):
+    """Uploads footprint patterns int8 [patterns, 32, 9] for MODE_SPARSE9 (pattern = frame % patterns)."""
+    import numpy as np
+    t = np.ascontiguousarray(table, np.int8)
+    assert t.ndim == 3 and t.shape[1:] == (32, 9)
+    _check(load().stf_set_sparse_footprints(t.ctypes.data, int(t.shape[0]), int(tile[0]), int(tile[1])))
