@@ -360,6 +360,10 @@ def run_ours(a):
         extras = {}
         refs = {}
         modes = dict(MODES, **(EXACT_MODES if a.filter == "bilinear" else {}))
+        # pseudorandom sparse 9-lane footprints, 8 patterns from the paper's generator settings
+        tab, _ = stf.sparse_footprints(tile=(8, 4), patterns=8, seed=0)
+        stf.set_sparse_footprints(tab, (8, 4))
+        modes["sparse9"] = stf.MODE_SPARSE9
         for name, m in modes.items():
             tt = time_mode(stf, torch, tex, view, m, max(5, a.steps // 2), 3, flush, rank, out)
             med = statistics.median(tt)
