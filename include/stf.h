@@ -68,6 +68,12 @@ typedef enum {
  * are rarely all drawn, Section "Exact Filtering"). With FULL or ONE_TAP: STF_ERR_INVALID_ARG. */
 #define STF_MODE_FLAG_EXACT 16
 
+/* Blue-noise selection uniforms (Section "Blue Noise Mask Improvements"), OR'd into any mode but
+ * FULL: a pixel's two uniforms are its ranks r in the two masks set by stf_set_blue_noise, at
+ * (x mod n, y mod n), as (r + 1/2) / n^2 plus the frame's offset frame * (sqrt(5) - 1) / 2 + the
+ * seed's low 24 bits / 2^24, modulo 1 (all in 24-bit fixed point) instead of the pcg4d hash. */
+#define STF_MODE_FLAG_BLUE_NOISE 32
+
 /* The estimator of a sharing mode, reuse_mode | (estimator << STF_MODE_EST_SHIFT), over the
  * footprint's samples x_i (drawn from the PMFs p_i = lane i's filter weights), with
  * f(x) = w_c(x) T(x) for the pixel's own filter w_c (Section 4.1 and Section 4.2):
@@ -255,6 +261,18 @@ stf_status stf_sparse_footprints(int tile_w, int tile_h, int count, double sigma
  * STF_ERR_INVALID_ARG for a malformed table (nothing changes). */
 #define STF_SPARSE_MAX_PATTERNS 256
 stf_status stf_set_sparse_footprints(const signed char* table, int patterns, int tile_w, int tile_h);
+
+/* Blue-noise masks (Section "Blue Noise Mask Improvements"): two independent scalar masks of
+ * size x size (a power of two, 4..256) made with the void-and-cluster method on the torus
+ * (Gaussian energy of standard deviation `sigma` pixels); with quad_energy != 0 the energy a pixel
+ * splats onto the other pixels of its aligned 2x2 quad is doubled (the paper's modification for
+ * quad sharing). ranks[2][size][size] (host) receives each pixel's rank 0 .. size^2 - 1.
+ * Deterministic for a seed. Host only, synchronous. */
+stf_status stf_blue_noise_masks(int size, double sigma, int quad_energy, unsigned long long seed, uint16_t* ranks);
+/* Sets the current device's masks for STF_MODE_FLAG_BLUE_NOISE: ranks[2][size][size] (host),
+ * each mask a permutation of 0 .. size^2 - 1. Waits for the device, may allocate device memory.
+ * Errors: STF_ERR_INVALID_ARG (nothing changes). */
+stf_status stf_set_blue_noise(const uint16_t* ranks, int size);
 
 /* Frees a texture (NULL is a no-op). The caller ensures no enqueued work still reads it. */
 stf_status stf_destroy(stf_texture* tex);

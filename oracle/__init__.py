@@ -26,6 +26,7 @@ LIB = os.path.join(HERE, "_build", "liboracle.so")
 BILINEAR, BSPLINE3 = 0, 1
 FULL, ONE_TAP, QUAD2, WAVE2, WAVE3, WAVE4, SPARSE9 = 0, 1, 2, 3, 4, 5, 6
 FLAG_EXACT = 16  # exact filtering (bilinear), OR'd into a sharing mode
+FLAG_BLUE = 32  # blue-noise uniforms from the view's masks
 EST_SHIFT, FLAG_CLAMP = 8, 2048  # alternative estimators: mode | (est << EST_SHIFT) [| FLAG_CLAMP]
 EST_WIS, EST_IS, EST_MIS, EST_PMIS, EST_REG = range(5)
 
@@ -75,6 +76,7 @@ class RefView(C.Structure):
         ("ch_ao", C.c_int), ("roughness", C.c_float), ("filter", C.c_int),
         ("tile_w", C.c_int), ("tile_h", C.c_int), ("frame", C.c_int), ("view_id", C.c_int),
         ("fp_table", C.c_void_p), ("fp_patterns", C.c_int),
+        ("blue", C.c_void_p), ("blue_size", C.c_int),
     ]
 
 
@@ -315,6 +317,12 @@ def _view_struct(view):
         v._fp = fp  # kept alive with the struct
         v.fp_table = fp.ctypes.data
         v.fp_patterns = fp.shape[0]
+    blue = view.get("blue")  # uint16 ranks [2, n, n] for FLAG_BLUE
+    if blue is not None:
+        blue = np.ascontiguousarray(blue, np.uint16)
+        v._blue = blue
+        v.blue = blue.ctypes.data
+        v.blue_size = blue.shape[1]
     return v
 
 

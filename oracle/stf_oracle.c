@@ -448,6 +448,7 @@ typedef struct {
     int mode;                /* sharing mode without flags */
     int exact;               /* REF_FLAG_EXACT given */
     int est, clamp;          /* REF_EST_*, REF_FLAG_CLAMP given */
+    int blue;                /* REF_FLAG_BLUE given */
     uint64_t seed;
     float* out_rgba;
     uint32_t* out_idx;
@@ -493,6 +494,20 @@ static int full_filter(const ref_material* m, int f, int C, float cx, float cy, 
     }
     for (int c = 0; c < C; ++c) res[c] = acc[c];
     return 1;
+}
+
+/* Blue-noise uniforms of pixel (x, y) (REF_FLAG_BLUE in the header). */
+static void blue_uniforms(const ref_view* v, int x, int y, uint64_t seed, float* ux, float* uy)
+{
+    const uint32_t n = (uint32_t)v->blue_size, N = n * n;
+    const uint32_t S = (1u << 24) / N; /* 2^24 / n^2, n a power of two */
+    const uint32_t fold = ((uint32_t)seed ^ (uint32_t)(seed >> 32)) & 0xffffffu;
+    const uint32_t off = ((uint32_t)v->frame * 10368890u + fold) & 0xffffffu;
+    const uint32_t k = ((uint32_t)y % n) * n + (uint32_t)x % n;
+    const uint32_t a = ((uint32_t)v->blue[k] * S + S / 2 + off) & 0xffffffu;
+    const uint32_t b = ((uint32_t)v->blue[N + k] * S + S / 2 + off) & 0xffffffu;
+    *ux = (float)a * (1.0f / 16777216.0f);
+    *uy = (float)b * (1.0f / 16777216.0f);
 }
 
 /* The footprint of a lane: the square footprints of the sharing modes, or the lane's row of the
@@ -615,7 +630,8 @@ static void render_tile(const job_t* J, int tx, int ty)
         stf_ref_texel_coords(v, m->width, m->height, px[lane], py[lane], &cx[lane], &cy[lane]);
         if (J->mode == REF_FULL) continue;
         float ux, uy, wx, wy;
-        stf_ref_uniforms(px[lane], py[lane], v->frame, v->view_id, J->seed, &ux, &uy);
+        if (J->blue) blue_uniforms(v, px[lane], py[lane], J->seed, &ux, &uy);
+        else stf_ref_uniforms(px[lane], py[lane], v->frame, v->view_id, J->seed, &ux, &uy);
         stf_ref_select_axis(f, cx[lane], ux, &ix[lane], &wx);
         stf_ref_select_axis(f, cy[lane], uy, &iy[lane], &wy);
         /* the PMF of the chosen texel is its 2D filter weight */
@@ -725,7 +741,13 @@ int stf_ref_render(const ref_material* m, const ref_view* v, int mode, uint64_t 
     const int exact = (mode & REF_FLAG_EXACT) != 0;
     const int est = (mode >> REF_EST_SHIFT) & 7;
     const int clamp = (mode & REF_FLAG_CLAMP) != 0;
+    const int blue = (mode & REF_FLAG_BLUE) != 0;
     mode &= 15;
+    if (blue) {
+        if (mode == REF_FULL || !v->blue || v->blue_size < 4 || v->blue_size > 256 ||
+            (v->blue_size & (v->blue_size - 1)))
+            return 1;
+    }
     if (mode < REF_FULL || mode > REF_SPARSE9) return 1;
     if (mode == REF_SPARSE9) {
         if (!v->fp_table || v->fp_patterns < 1) return 1;
@@ -738,7 +760,7 @@ int stf_ref_render(const ref_material* m, const ref_view* v, int mode, uint64_t 
     if (mode == REF_QUAD2 && (v->tile_w % 2 || v->tile_h % 2)) return 1;
     job_t J;
     memset(&J, 0, sizeof J);
-    J.m = m; J.v = v; J.mode = mode; J.exact = exact; J.est = est; J.clamp = clamp; J.seed = seed;
+    J.m = m; J.v = v; J.mode = mode; J.exact = exact; J.est = est; J.clamp = clamp; J.blue = blue; J.seed = seed;
     J.out_rgba = out_rgba; J.out_idx = out_idx; J.out_ch = out_ch;
     return run_jobs(&J, nthreads);
 }

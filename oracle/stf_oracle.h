@@ -35,6 +35,12 @@ enum { REF_FULL = 0, REF_ONE_TAP = 1, REF_QUAD2 = 2, REF_WAVE2 = 3, REF_WAVE3 = 
  * returns the deterministic filter over those texels instead of the estimate. */
 #define REF_FLAG_EXACT 16
 
+/* Blue-noise uniforms (Section "Blue Noise Mask Improvements"), OR'd into a mode: the pixel's
+ * uniforms are its ranks r in the view's two masks at (x mod n, y mod n), u = (r + 1/2) / n^2 +
+ * frame * (sqrt(5) - 1) / 2 + (seed's folded low 24 bits) / 2^24 modulo 1, in 24-bit fixed point
+ * (the golden-ratio step rounded to 10368890 / 2^24). */
+#define REF_FLAG_BLUE 32
+
 /* The estimator of a sharing mode, (mode >> REF_EST_SHIFT) & 7 (Section 4.1 and Section 4.2),
  * over the footprint's samples x_i drawn from the PMFs p_i (lane i's filter weights), with
  * f(x) = w_c(x) T(x) for the pixel's own filter w_c:
@@ -95,6 +101,9 @@ typedef struct {
     /* REF_SPARSE9: fp_table[fp_patterns][32][9] lane indices (own lane first), else NULL */
     const signed char* fp_table;
     int fp_patterns;
+    /* blue-noise uniforms (REF_FLAG_BLUE): ranks [2][blue_size][blue_size], else NULL */
+    const uint16_t* blue;
+    int blue_size;
 } ref_view;
 
 /* Counter-based hash (pcg4d, Jarzynski and Olano 2020), in place. */

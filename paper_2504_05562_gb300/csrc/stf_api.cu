@@ -85,6 +85,8 @@ struct DeviceState {
     int* flags = nullptr;        // [0] timeout, [1] device assert
     uint8_t* fp = nullptr;       // sparse footprint patterns [fp_patterns][32][16] (STF_MODE_SPARSE9)
     int fp_patterns = 0, fp_capacity = 0, fp_tw = 0, fp_th = 0;
+    uint16_t* blue = nullptr;    // blue-noise ranks [2][n][n] (STF_MODE_FLAG_BLUE_NOISE)
+    int blue_shift = 0, blue_capacity = 0;
 };
 static DeviceState g_dev[64];
 
@@ -105,6 +107,49 @@ bool stf_sparse_state(const uint8_t** table, int* patterns, int* tile_w, int* ti
     if (tile_w) *tile_w = d->fp_tw;
     if (tile_h) *tile_h = d->fp_th;
     return true;
+}
+
+// The current device's blue-noise masks: false if none were set.
+bool stf_blue_state(const uint16_t** ranks, int* shift)
+{
+    const DeviceState* d = current_state();
+    if (!d || !d->blue) return false;
+    if (ranks) *ranks = d->blue;
+    if (shift) *shift = d->blue_shift;
+    return true;
+}
+
+extern "C" stf_status stf_set_blue_noise(const uint16_t* ranks, int size)
+{
+    int shift = 0;
+    while ((1 << shift) < size) ++shift;
+    if (!ranks || size < 4 || size > 256 || (1 << shift) != size)
+        return stf_fail(STF_ERR_INVALID_ARG, "stf_set_blue_noise: size %d (a power of two, 4..256)", size);
+    const int N = size * size;
+    for (int c = 0; c < 2; ++c) {  // each mask a permutation of the ranks 0 .. size^2 - 1
+        std::vector<uint8_t> seen((size_t)N, 0);
+        for (int i = 0; i < N; ++i) {
+            const int r = ranks[(size_t)c * N + i];
+            if (r >= N || seen[r]) return stf_fail(STF_ERR_INVALID_ARG, "stf_set_blue_noise: mask %d is not a permutation", c);
+            seen[r] = 1;
+        }
+    }
+    stf_status st = stf_device_state(nullptr, nullptr);
+    if (st != STF_OK) return st;
+    DeviceState& d = *current_state();
+    cudaError_t e;
+    if (2 * N > d.blue_capacity) {
+        if (d.blue && (e = cudaFree(d.blue)) != cudaSuccess) return stf_cuda_fail(e, "cudaFree(blue noise)");
+        d.blue = nullptr;
+        d.blue_capacity = 0;
+        if ((e = cudaMalloc(&d.blue, (size_t)2 * N * sizeof(uint16_t))) != cudaSuccess) return stf_cuda_fail(e, "cudaMalloc(blue noise)");
+        d.blue_capacity = 2 * N;
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return stf_cuda_fail(e, "synchronize");
+    if ((e = cudaMemcpy(d.blue, ranks, (size_t)2 * N * sizeof(uint16_t), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return stf_cuda_fail(e, "cudaMemcpy(blue noise)");
+    d.blue_shift = shift;
+    return STF_OK;
 }
 
 extern "C" stf_status stf_set_sparse_footprints(const signed char* table, int patterns, int tile_w, int tile_h)
@@ -413,6 +458,8 @@ stf_status stf_validate_view(const stf_view& v, int i, int filter, int mode)
     }
     for (int k = 0; k < 9; ++k)
         if (!std::isfinite(v.H[k])) return stf_fail(STF_ERR_INVALID_ARG, "view %d: H[%d] not finite", i, k);
+    if ((mode & STF_MODE_FLAG_BLUE_NOISE) && !stf_blue_state(nullptr, nullptr))
+        return stf_fail(STF_ERR_INVALID_ARG, "view %d: STF_MODE_FLAG_BLUE_NOISE without stf_set_blue_noise", i);
     if ((mode & kModeBase) == STF_MODE_SPARSE9) {
         int tw = 0, th = 0;
         if (!stf_sparse_state(nullptr, nullptr, &tw, &th))
@@ -471,6 +518,15 @@ void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long lon
     stf_device_state(&d.flags, nullptr);
     d.affine = (v.H[6] == 0.0f && v.H[7] == 0.0f && v.H[8] == 1.0f) ? 1 : 0;
     d.estimator = ((mode >> STF_MODE_EST_SHIFT) & 7) | ((mode & STF_MODE_FLAG_CLAMP) ? 8 : 0);
+    if (mode & STF_MODE_FLAG_BLUE_NOISE) {
+        const uint16_t* r = nullptr;
+        int sh = 0;
+        if (stf_blue_state(&r, &sh)) {
+            d.blue = r;
+            d.blue_shift = sh;
+            d.blue_offset = ((uint32_t)v.frame * kBlueFrameStep + (d.rng_w & 0xffffffu)) & 0xffffffu;
+        }
+    }
     if (!v.shading) d.shade_layout = 0;
     else if (v.ch_albedo == 0 && v.ch_normal == 3 && v.ch_rough == 5 && v.ch_ao == 6) d.shade_layout = 1;
     else if (v.ch_albedo == 0 && v.ch_normal == 4 && v.ch_rough == -1 && v.ch_ao == -1) d.shade_layout = 2;
@@ -508,11 +564,13 @@ stf_status stf_check_mode(int mode)
 {
     const int base = mode & kModeBase;
     const int est = (mode >> STF_MODE_EST_SHIFT) & 7;
-    const int known = kModeBase | STF_MODE_FLAG_EXACT | (7 << STF_MODE_EST_SHIFT) | STF_MODE_FLAG_CLAMP;
+    const int known = kModeBase | STF_MODE_FLAG_EXACT | STF_MODE_FLAG_BLUE_NOISE | (7 << STF_MODE_EST_SHIFT) | STF_MODE_FLAG_CLAMP;
     if (base > STF_MODE_SPARSE9 || (mode & ~known) || est > STF_EST_REGRESSION)
         return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d", mode);
     if ((mode & STF_MODE_FLAG_EXACT) && base < STF_MODE_QUAD2)
         return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: exact filtering needs a sharing mode", mode);
+    if ((mode & STF_MODE_FLAG_BLUE_NOISE) && base == STF_MODE_FULL)
+        return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: the full filter draws no random numbers", mode);
     if ((est || (mode & STF_MODE_FLAG_CLAMP)) && base < STF_MODE_QUAD2)
         return stf_fail(STF_ERR_INVALID_ARG, "reuse_mode %d: an estimator needs a sharing mode", mode);
     if ((mode & STF_MODE_FLAG_CLAMP) && est == STF_EST_WIS)

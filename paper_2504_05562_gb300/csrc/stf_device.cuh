@@ -27,6 +27,8 @@ constexpr int kModeEstShift = 8;     // STF_MODE_EST_SHIFT: (mode >> 8) & 7 = th
 constexpr int kModeFlagClamp = 2048; // STF_MODE_FLAG_CLAMP
 constexpr int kModeBase = 15;        // the stf_reuse_mode bits
 constexpr int kModeSparse9 = 6;      // STF_MODE_SPARSE9: 9-element pseudorandom sparse footprints
+constexpr int kModeFlagBlue = 32;    // STF_MODE_FLAG_BLUE_NOISE
+constexpr uint32_t kBlueFrameStep = 10368890u;  // round(2^24 (sqrt(5) - 1) / 2): the golden-ratio step
 constexpr int kBatchMaxViews = 224; // views per persistent launch (their constants sit in a constant bank)
 
 // Material kinds with a dedicated kernel. Anything else is widened to FP32 at creation.
@@ -71,6 +73,9 @@ struct DevView {
     const void* neural;       // decoder parameters for K_NEURAL
     int* flags;               // device error counters: [0] timed-out waits
     const uint8_t* fp;        // STF_MODE_SPARSE9: the frame's pattern, [32 lanes][16] lane indices
+    const uint16_t* blue;     // STF_MODE_FLAG_BLUE_NOISE: ranks [2][n][n] (n = 1 << blue_shift), else null
+    int blue_shift;
+    uint32_t blue_offset;     // 24-bit offset of the frame: frame * golden-ratio step + seed (mod 2^24)
     int estimator;            // alternative estimator (kernels compiled with ALT): 1 IS, 2 MIS,
                               // 3 pairwise MIS, 4 regression; + 8: clamp to the texels' range
 };
@@ -195,6 +200,30 @@ template <int F> __device__ __forceinline__ void axis_select(float c, float u, A
     A.n = A.base + pick;
     A.nf = __fadd_rn(A.basef, __int2float_rn(pick));
     A.p = p;
+}
+
+// The pixel's two selection uniforms as exact 24-bit dyadic floats: the counter hash pcg4d of
+// (x, y, frame | view << 16, seed), or, with blue-noise masks, the ranks r of (x mod n, y mod n)
+// in two independent masks as (r + 1/2) / n^2 shifted by the frame's offset modulo 1 (a
+// golden-ratio step per frame, Cranley-Patterson rotation).
+__device__ __forceinline__ void pixel_uniforms(const DevView& v, int x, int y, float& ux, float& uy)
+{
+    uint32_t a, b;
+    if (v.blue) {
+        const int n = 1 << v.blue_shift, m = n - 1;
+        const int k = ((y & m) << v.blue_shift) | (x & m);
+        const uint32_t step = 24 - 2 * v.blue_shift;  // 2^24 / n^2 = 1 << step
+        const uint32_t half = step > 0 ? 1u << (step - 1) : 0u;
+        a = (((uint32_t)__ldg(v.blue + k) << step) + half + v.blue_offset) & 0xffffffu;
+        b = (((uint32_t)__ldg(v.blue + (n << v.blue_shift) + k) << step) + half + v.blue_offset) & 0xffffffu;
+    } else {
+        uint32_t ra = (uint32_t)x, rb = (uint32_t)y, rc = v.rng_z, rd = v.rng_w;
+        pcg4d(ra, rb, rc, rd);
+        a = ra >> 8;
+        b = rb >> 8;
+    }
+    ux = __uint2float_rn(a) * (1.0f / 16777216.0f);
+    uy = __uint2float_rn(b) * (1.0f / 16777216.0f);
 }
 
 // ------------------------------------------------------------------------------ coordinates

@@ -39,6 +39,9 @@ stf_status stf_check_mode(int mode);
 // The current device's sparse footprint patterns (stf_set_sparse_footprints); false if none.
 bool stf_sparse_state(const uint8_t** table, int* patterns, int* tile_w, int* tile_h);
 
+// The current device's blue-noise masks (stf_set_blue_noise); false if none.
+bool stf_blue_state(const uint16_t** ranks, int* shift);
+
 // resident blocks per SM, counted from the kernel's resources (stf_api.cu)
 cudaError_t stf_resident_blocks(const void* kernel, int threads, int dyn_bytes, int* n);
 

@@ -68,10 +68,8 @@ struct NnRenderClient {
                 rec = make_float4(__fmul_rn(wx, wy), 0.0f, 0.0f, 0.0f);
             } else {
                 // one texel drawn from the pixel's filter PMF (Section 2.2, Section S1)
-                uint32_t ra = (uint32_t)x, rb = (uint32_t)y, rc = v.rng_z, rd = v.rng_w;
-                pcg4d(ra, rb, rc, rd);
-                const float ux = __uint2float_rn(ra >> 8) * (1.0f / 16777216.0f);
-                const float uy = __uint2float_rn(rb >> 8) * (1.0f / 16777216.0f);
+                float ux, uy;
+                pixel_uniforms(v, x, y, ux, uy);
                 Axis<F> ax, ay;
                 axis_select<F>(cx, ux, ax);
                 axis_select<F>(cy, uy, ay);

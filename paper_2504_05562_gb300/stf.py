@@ -17,6 +17,7 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, 
 FILTER_BILINEAR, FILTER_BSPLINE3, FILTER_PER_VIEW = 0, 1, -1
 MODE_FULL, MODE_ONE_TAP, MODE_QUAD2, MODE_WAVE2, MODE_WAVE3, MODE_WAVE4, MODE_SPARSE9 = range(7)
 MODE_FLAG_EXACT = 16  # exact filtering (bilinear), OR'd into a sharing mode
+MODE_FLAG_BLUE_NOISE = 32  # blue-noise selection uniforms (stf_set_blue_noise)
 # alternative estimators (evaluation modes): mode | (EST_* << MODE_EST_SHIFT) [| MODE_FLAG_CLAMP]
 MODE_EST_SHIFT, MODE_FLAG_CLAMP = 8, 2048
 EST_WIS, EST_IS, EST_MIS, EST_PAIRWISE_MIS, EST_REGRESSION = range(5)
@@ -57,7 +58,8 @@ EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_str
            "stf_decoder_get_params", "stf_decoder_set_params", "stf_decoder_decode", "stf_decoder_info",
            "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy", "stf_set_option", "stf_get_stat",
            "stf_autotune", "stf_view_config", "stf_autotune_save", "stf_autotune_load", "stf_autotune_clear",
-           "stf_render_views_noalloc", "stf_sparse_footprints", "stf_set_sparse_footprints")
+           "stf_render_views_noalloc", "stf_sparse_footprints", "stf_set_sparse_footprints",
+           "stf_blue_noise_masks", "stf_set_blue_noise")
 NOALLOC_MAX_VIEWS, NOALLOC_MAX_ITEMS = 224, 262144
 OPT_BATCH_GRAPHS = 1
 STAT_GRAPH_BUILDS, STAT_GRAPH_REPLAYS = 1, 2
@@ -101,6 +103,8 @@ def _bind_extra(L):
     L.stf_autotune_clear.argtypes = []
     L.stf_render_views_noalloc.argtypes = [C.POINTER(View), C.c_int, C.c_int, C.c_int, C.c_ulonglong]
     L.stf_set_sparse_footprints.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.stf_blue_noise_masks.argtypes = [C.c_int, C.c_double, C.c_int, C.c_ulonglong, C.c_void_p]
+    L.stf_set_blue_noise.argtypes = [C.c_void_p, C.c_int]
     L.stf_sparse_footprints.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
                                         C.c_ulonglong, C.c_int, C.c_void_p, C.c_void_p]
     for n in ("stf_set_option", "stf_get_stat", "stf_autotune", "stf_view_config", "stf_autotune_save",
@@ -306,3 +310,22 @@ def set_sparse_footprints(table, tile=(8, 4)):
     t = np.ascontiguousarray(table, np.int8)
     assert t.ndim == 3 and t.shape[1:] == (32, 9)
     _check(load().stf_set_sparse_footprints(t.ctypes.data, int(t.shape[0]), int(tile[0]), int(tile[1])))
+
+
+# ----------------------------------------------------------------------------- blue noise
+
+def blue_noise_masks(size=64, sigma=1.5, quad_energy=True, seed=0):
+    """Two void-and-cluster blue-noise masks: uint16 ranks [2, size, size] (host code)."""
+    import numpy as np
+    r = np.zeros((2, size, size), np.uint16)
+    _check(load().stf_blue_noise_masks(int(size), float(sigma), 1 if quad_energy else 0, int(seed) & (2 ** 64 - 1),
+                                       r.ctypes.data))
+    return r
+
+
+def set_blue_noise(ranks):
+    """Uploads masks uint16 [2, n, n] for MODE_FLAG_BLUE_NOISE."""
+    import numpy as np
+    r = np.ascontiguousarray(ranks, np.uint16)
+    assert r.ndim == 3 and r.shape[0] == 2 and r.shape[1] == r.shape[2]
+    _check(load().stf_set_blue_noise(r.ctypes.data, int(r.shape[1])))
