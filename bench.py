@@ -364,6 +364,10 @@ def run_ours(a):
         tab, _ = stf.sparse_footprints(tile=(8, 4), patterns=8, seed=0)
         stf.set_sparse_footprints(tab, (8, 4))
         modes["sparse9"] = stf.MODE_SPARSE9
+        # blue-noise uniforms (void-and-cluster masks with the doubled intra-quad energy)
+        stf.set_blue_noise(stf.blue_noise_masks(64, seed=0))
+        for name in ("one_tap", "quad2", "wave3"):
+            modes[name + "_blue"] = MODES[name] | stf.MODE_FLAG_BLUE_NOISE
         for name, m in modes.items():
             tt = time_mode(stf, torch, tex, view, m, max(5, a.steps // 2), 3, flush, rank, out)
             med = statistics.median(tt)
