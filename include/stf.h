@@ -231,7 +231,8 @@ stf_status stf_autotune_clear(void);
  * enqueued); work items are coarsened to fit STF_NOALLOC_MAX_ITEMS, which changes no pixel;
  * neural-texture views of one call must share one decoder (else STF_ERR_INVALID_ARG).
  * The first call on a device looks up the array's device address and uploads a 1 KB table with
- * a blocking copy: make it before any stream capture. All calls share the array (the counters
+ * a blocking copy, and, unless another entry point ran on the device before, sets up the
+ * library's per-device state (error flags, allocated once): make it before any stream capture. All calls share the array (the counters
  * are cleared on each call): calls that overlap on the GPU race. Asynchronous on the library
  * stream otherwise. */
 #define STF_NOALLOC_MAX_VIEWS 224

@@ -518,14 +518,12 @@ void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long lon
     stf_device_state(&d.flags, nullptr);
     d.affine = (v.H[6] == 0.0f && v.H[7] == 0.0f && v.H[8] == 1.0f) ? 1 : 0;
     d.estimator = ((mode >> STF_MODE_EST_SHIFT) & 7) | ((mode & STF_MODE_FLAG_CLAMP) ? 8 : 0);
-    if (mode & STF_MODE_FLAG_BLUE_NOISE) {
-        const uint16_t* r = nullptr;
-        int sh = 0;
-        if (stf_blue_state(&r, &sh)) {
-            d.blue = r;
-            d.blue_shift = sh;
-            d.blue_offset = ((uint32_t)v.frame * kBlueFrameStep + (d.rng_w & 0xffffffu)) & 0xffffffu;
-        }
+    const uint16_t* r = nullptr;
+    int sh = 0;
+    if ((mode & STF_MODE_FLAG_BLUE_NOISE) && stf_blue_state(&r, &sh)) {
+        d.blue = r;
+        d.blue_shift = sh;
+        d.blue_offset = ((uint32_t)v.frame * kBlueFrameStep + (d.rng_w & 0xffffffu)) & 0xffffffu;
     }
     if (!v.shading) d.shade_layout = 0;
     else if (v.ch_albedo == 0 && v.ch_normal == 3 && v.ch_rough == 5 && v.ch_ao == 6) d.shade_layout = 1;

@@ -73,7 +73,7 @@ struct DevView {
     const void* neural;       // decoder parameters for K_NEURAL
     int* flags;               // device error counters: [0] timed-out waits
     const uint8_t* fp;        // STF_MODE_SPARSE9: the frame's pattern, [32 lanes][16] lane indices
-    const uint16_t* blue;     // STF_MODE_FLAG_BLUE_NOISE: ranks [2][n][n] (n = 1 << blue_shift), else null
+    const uint16_t* blue;     // STF_MODE_FLAG_BLUE_NOISE: ranks [2][n][n] (n = 1 << blue_shift)
     int blue_shift;
     uint32_t blue_offset;     // 24-bit offset of the frame: frame * golden-ratio step + seed (mod 2^24)
     int estimator;            // alternative estimator (kernels compiled with ALT): 1 IS, 2 MIS,
@@ -203,19 +203,21 @@ template <int F> __device__ __forceinline__ void axis_select(float c, float u, A
 }
 
 // The pixel's two selection uniforms as exact 24-bit dyadic floats: the counter hash pcg4d of
-// (x, y, frame | view << 16, seed), or, with blue-noise masks, the ranks r of (x mod n, y mod n)
-// in two independent masks as (r + 1/2) / n^2 shifted by the frame's offset modulo 1 (a
-// golden-ratio step per frame, Cranley-Patterson rotation).
+// (x, y, frame | view << 16, seed), or (BLUE) the ranks r of (x mod n, y mod n) in two
+// independent blue-noise masks as (r + 1/2) / n^2 shifted by the frame's offset modulo 1 (a
+// golden-ratio step per frame, Cranley-Patterson rotation). BLUE is a kernel variant: a runtime
+// choice here costs the render kernels registers, and spills, in their sharing loops.
+template <bool BLUE>
 __device__ __forceinline__ void pixel_uniforms(const DevView& v, int x, int y, float& ux, float& uy)
 {
     uint32_t a, b;
-    if (v.blue) {
-        const int n = 1 << v.blue_shift, m = n - 1;
-        const int k = ((y & m) << v.blue_shift) | (x & m);
-        const uint32_t step = 24 - 2 * v.blue_shift;  // 2^24 / n^2 = 1 << step
-        const uint32_t half = step > 0 ? 1u << (step - 1) : 0u;
+    if constexpr (BLUE) {
+        const int sh = v.blue_shift, m = (1 << sh) - 1;
+        const int k = ((y & m) << sh) | (x & m);
+        const uint32_t step = 24 - 2 * sh;  // 2^24 / n^2 = 1 << step
+        const uint32_t half = (1u << step) >> 1;
         a = (((uint32_t)__ldg(v.blue + k) << step) + half + v.blue_offset) & 0xffffffu;
-        b = (((uint32_t)__ldg(v.blue + (n << v.blue_shift) + k) << step) + half + v.blue_offset) & 0xffffffu;
+        b = (((uint32_t)__ldg(v.blue + ((m + 1) << sh) + k) << step) + half + v.blue_offset) & 0xffffffu;
     } else {
         uint32_t ra = (uint32_t)x, rb = (uint32_t)y, rc = v.rng_z, rd = v.rng_w;
         pcg4d(ra, rb, rc, rd);

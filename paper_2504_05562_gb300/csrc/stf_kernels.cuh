@@ -170,7 +170,7 @@ __device__ __forceinline__ void alt_combine(int est, int lane, float cx, float c
 // weighted one (v.estimator).
 // All 32 lanes execute every shuffle (off-screen lanes of a partial tile compute with
 // extrapolated coordinates and only skip the store).
-template <int KIND, int F, int MODE, int TW, int TH, bool EX = false, bool ALT = false>
+template <int KIND, int F, int MODE, int TW, int TH, bool EX = false, bool ALT = false, bool BLUE = false>
 __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, int lane, float4* rec, float* wtab)
 {
     constexpr int C = Channels<KIND>::C;
@@ -205,7 +205,7 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
     } else {
         // one-tap STF: one texel drawn from the lane's own filter PMF (Section 2.2, Section S1)
         float ux, uy;
-        pixel_uniforms(v, x, y, ux, uy);
+        pixel_uniforms<BLUE>(v, x, y, ux, uy);
         Axis<F> ax, ay;
         axis_select<F>(cx, ux, ax);
         axis_select<F>(cy, uy, ay);
@@ -337,7 +337,7 @@ constexpr int kRecPerLane = 3;
 constexpr int kMinBlocks = 5;
 
 // One view: block (bx, by) holds 8 warps on tile row by, tiles bx * 8 .. bx * 8 + 7.
-template <int KIND, int F, int MODE, int TW, int TH, bool EX = false, bool ALT = false>
+template <int KIND, int F, int MODE, int TW, int TH, bool EX = false, bool ALT = false, bool BLUE = false>
 __global__ void __launch_bounds__(256, kMinBlocks) k_render_view(const DevView v)
 {
     constexpr int RPL = ALT ? 4 : kRecPerLane;
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) k_render_view(const DevView v
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tx = blockIdx.x * kWarpsPerBlock + warp;
     if (tx >= v.tiles_x) return;  // warp-uniform
-    render_tile<KIND, F, MODE, TW, TH, EX, ALT>(v, tx, blockIdx.y, lane, recs + warp * 32 * RPL, wtabs + warp * 32 * 8);
+    render_tile<KIND, F, MODE, TW, TH, EX, ALT, BLUE>(v, tx, blockIdx.y, lane, recs + warp * 32 * RPL, wtabs + warp * 32 * 8);
 }
 
 }  // namespace stf

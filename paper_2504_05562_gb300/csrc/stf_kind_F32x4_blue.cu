@@ -1,0 +1,3 @@
+// Render kernels for material kind K_F32x4 with blue-noise selection uniforms.
+#include "stf_launch.cuh"
+STF_INSTANTIATE_KIND_BLUE(stf::K_F32x4, launch_view_F32x4)

@@ -37,7 +37,7 @@ static int device_sms()
     return n > 0 ? n : 1;
 }
 
-template <int KIND, int F, int MODE, int TW, int TH, bool EX = false, bool ALT = false>
+template <int KIND, int F, int MODE, int TW, int TH, bool EX, bool ALT, bool BLUE>
 static cudaError_t launch_one(const DevView& v, cudaStream_t s)
 {
     const dim3 grid((unsigned)((v.tiles_x + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)v.tiles_y);
@@ -46,62 +46,62 @@ static cudaError_t launch_one(const DevView& v, cudaStream_t s)
         static int cached = 0;
         int per_sm = 1;
         constexpr int dyn = (int)sizeof(NnPipeSmem);
-        cudaError_t e = prepare_dynamic(k_render_neural<F, MODE, TW, TH, EX>, dyn, kNnPipeThreads, cached, &per_sm);
+        cudaError_t e = prepare_dynamic(k_render_neural<F, MODE, TW, TH, EX, BLUE>, dyn, kNnPipeThreads, cached, &per_sm);
         if (e != cudaSuccess) return e;
         const long long groups = (long long)((v.tiles_x + kNnClientWarps - 1) / kNnClientWarps) * v.tiles_y;
         const unsigned blocks = (unsigned)(groups < (long long)per_sm * device_sms() ? groups : (long long)per_sm * device_sms());
-        k_render_neural<F, MODE, TW, TH, EX><<<blocks, kNnPipeThreads, dyn, s>>>(v);
+        k_render_neural<F, MODE, TW, TH, EX, BLUE><<<blocks, kNnPipeThreads, dyn, s>>>(v);
     } else {
-        k_render_view<KIND, F, MODE, TW, TH, EX, ALT><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
+        k_render_view<KIND, F, MODE, TW, TH, EX, ALT, BLUE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
     }
     return cudaGetLastError();
 }
 
-template <int KIND, int F, int MODE, bool EX>
+template <int KIND, int F, int MODE, bool EX, bool BLUE>
 static cudaError_t launch_tiles(const DevView& v, cudaStream_t s)
 {
-    if (v.tile_w == 8 && v.tile_h == 4) return launch_one<KIND, F, MODE, 8, 4, EX>(v, s);
-    if (v.tile_w == 4 && v.tile_h == 8) return launch_one<KIND, F, MODE, 4, 8, EX>(v, s);
-    if (v.tile_w == 16 && v.tile_h == 2) return launch_one<KIND, F, MODE, 16, 2, EX>(v, s);
+    if (v.tile_w == 8 && v.tile_h == 4) return launch_one<KIND, F, MODE, 8, 4, EX, false, BLUE>(v, s);
+    if (v.tile_w == 4 && v.tile_h == 8) return launch_one<KIND, F, MODE, 4, 8, EX, false, BLUE>(v, s);
+    if (v.tile_w == 16 && v.tile_h == 2) return launch_one<KIND, F, MODE, 16, 2, EX, false, BLUE>(v, s);
     return cudaErrorInvalidValue;
 }
 
 // Sharing modes; exact filtering exists for the bilinear filter (the B-spline ignores the flag);
 // the alternative estimators (v.estimator != 0) for stored kinds on 8x4 tiles.
-template <int KIND, int F, int MODE>
+template <int KIND, int F, int MODE, bool BLUE>
 static cudaError_t launch_sharing(const DevView& v, bool ex, cudaStream_t s)
 {
     if constexpr (KIND != K_NEURAL && MODE != kModeSparse9)
         if (v.estimator != 0) {
             if (v.tile_w != 8 || v.tile_h != 4) return cudaErrorInvalidValue;
-            return launch_one<KIND, F, MODE, 8, 4, false, true>(v, s);
+            return launch_one<KIND, F, MODE, 8, 4, false, true, BLUE>(v, s);
         }
     if constexpr (F == 0)
-        if (ex) return launch_tiles<KIND, F, MODE, true>(v, s);
-    return launch_tiles<KIND, F, MODE, false>(v, s);
+        if (ex) return launch_tiles<KIND, F, MODE, true, BLUE>(v, s);
+    return launch_tiles<KIND, F, MODE, false, BLUE>(v, s);
 }
 
-template <int KIND, int F>
+template <int KIND, int F, bool BLUE>
 static cudaError_t launch_modes(const DevView& v, int mode, cudaStream_t s)
 {
     const bool ex = (mode & kModeFlagExact) != 0;
     switch (mode & kModeBase) {
-    case 0: return launch_one<KIND, F, 0, 8, 4>(v, s);  // no sharing: tile shape irrelevant
-    case 1: return launch_one<KIND, F, 1, 8, 4>(v, s);
-    case 2: return launch_sharing<KIND, F, 2>(v, ex, s);
-    case 3: return launch_sharing<KIND, F, 3>(v, ex, s);
-    case 4: return launch_sharing<KIND, F, 4>(v, ex, s);
-    case 5: return launch_sharing<KIND, F, 5>(v, ex, s);
-    case 6: return launch_sharing<KIND, F, 6>(v, ex, s);
+    case 0: return launch_one<KIND, F, 0, 8, 4, false, false, false>(v, s);  // no sharing: tile shape irrelevant
+    case 1: return launch_one<KIND, F, 1, 8, 4, false, false, BLUE>(v, s);
+    case 2: return launch_sharing<KIND, F, 2, BLUE>(v, ex, s);
+    case 3: return launch_sharing<KIND, F, 3, BLUE>(v, ex, s);
+    case 4: return launch_sharing<KIND, F, 4, BLUE>(v, ex, s);
+    case 5: return launch_sharing<KIND, F, 5, BLUE>(v, ex, s);
+    case 6: return launch_sharing<KIND, F, 6, BLUE>(v, ex, s);
     }
     return cudaErrorInvalidValue;
 }
 
 // mode: the C interface's reuse mode, with STF_MODE_FLAG_EXACT (kModeFlagExact) allowed.
-template <int KIND>
+template <int KIND, bool BLUE>
 cudaError_t launch_view_kind(const DevView& v, int mode, cudaStream_t s)
 {
-    return v.filter == 0 ? launch_modes<KIND, 0>(v, mode, s) : launch_modes<KIND, 1>(v, mode, s);
+    return v.filter == 0 ? launch_modes<KIND, 0, BLUE>(v, mode, s) : launch_modes<KIND, 1, BLUE>(v, mode, s);
 }
 
 // ------------------------------------------------------------------------------ multi-view
@@ -115,7 +115,7 @@ static __constant__ DevView c_batch_views[kBatchMaxViews];
 // (a run of tiles of one view) from a device counter until the list is exhausted. Nothing waits
 // on another block, so no wait can stall. One kernel per variant keeps the code of a launch as
 // small as a single-view kernel's.
-template <int KIND, int MODE, int F, int TW, int TH, bool EX = false>
+template <int KIND, int MODE, int F, int TW, int TH, bool EX, bool BLUE>
 __global__ void __launch_bounds__(256, kMinBlocks)
     k_render_batch(const WorkItem* __restrict__ items, int n_items, int* counter)
 {
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256, kMinBlocks)
         for (int k = warp; k < w.ntiles; k += kWarpsPerBlock) {
             const int t = w.tile0 + k;
             const int ty = t / v.tiles_x;
-            render_tile<KIND, F, MODE, TW, TH, EX>(v, t - ty * v.tiles_x, ty, lane, rec, wtab);
+            render_tile<KIND, F, MODE, TW, TH, EX, false, BLUE>(v, t - ty * v.tiles_x, ty, lane, rec, wtab);
         }
     }
 }
@@ -150,7 +150,7 @@ struct NnConstViews {
 // The neural kind's multi-view kernel: the same work items, rendered by the client warps of the
 // decode pipeline (all of a batch's neural views share one decoder; view 0 names it). The client
 // warps pull items together (named barrier 1), so every client takes the same rounds.
-template <int MODE, int F, int TW, int TH, bool EX = false>
+template <int MODE, int F, int TW, int TH, bool EX, bool BLUE>
 __global__ void __launch_bounds__(kNnPipeThreads, 2)
     k_render_neural_batch(const WorkItem* __restrict__ items, int n_items, int* counter)
 {
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2)
         nn_decode_role(sm, c_batch_views[0].flags);
     } else {
         const int warp = threadIdx.x >> 5;
-        NnRenderClient<F, MODE, TW, TH, EX, NnConstViews> cl(sm, wtabs + warp * 256, NnConstViews{}, c_batch_views[0].flags);
+        NnRenderClient<F, MODE, TW, TH, EX, BLUE, NnConstViews> cl(sm, wtabs + warp * 256, NnConstViews{}, c_batch_views[0].flags);
 #pragma unroll 1
         for (;;) {
             if (threadIdx.x == 0) {
@@ -191,65 +191,65 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2)
 }
 
 // grid > 0 launches; grid == 0 only reports the instance's resident blocks per SM in *per_sm.
-template <int KIND, int MODE, int F, int TW, int TH, bool EX = false>
+template <int KIND, int MODE, int F, int TW, int TH, bool EX, bool BLUE>
 static cudaError_t launch_batch_v(const WorkItem* items, int n_items, int* counter, int grid, int* per_sm, cudaStream_t s)
 {
     if constexpr (KIND == K_NEURAL) {
         static int cached = 0;
         constexpr int dyn = (int)sizeof(NnPipeSmem);
         int n = 0;
-        cudaError_t e = prepare_dynamic(k_render_neural_batch<MODE, F, TW, TH, EX>, dyn, kNnPipeThreads, cached, &n);
+        cudaError_t e = prepare_dynamic(k_render_neural_batch<MODE, F, TW, TH, EX, BLUE>, dyn, kNnPipeThreads, cached, &n);
         if (e != cudaSuccess || grid == 0) {
             *per_sm = n;
             return e;
         }
-        k_render_neural_batch<MODE, F, TW, TH, EX><<<grid, kNnPipeThreads, dyn, s>>>(items, n_items, counter);
+        k_render_neural_batch<MODE, F, TW, TH, EX, BLUE><<<grid, kNnPipeThreads, dyn, s>>>(items, n_items, counter);
     } else {
         if (grid == 0)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE, F, TW, TH, EX>, 256, 0);
-        k_render_batch<KIND, MODE, F, TW, TH, EX><<<grid, 256, 0, s>>>(items, n_items, counter);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE, F, TW, TH, EX, BLUE>, 256, 0);
+        k_render_batch<KIND, MODE, F, TW, TH, EX, BLUE><<<grid, 256, 0, s>>>(items, n_items, counter);
     }
     return cudaGetLastError();
 }
 
 // variant = filter * 3 + tile shape (0: 8x4, 1: 4x8, 2: 16x2), + 6 for bilinear with exact
 // filtering; without sharing only 8x4 exists.
-template <int KIND, int MODE>
+template <int KIND, int MODE, bool BLUE>
 static cudaError_t launch_batch_mode(const WorkItem* items, int n_items, int* counter, int grid, int variant, int* per_sm,
                                      cudaStream_t s)
 {
     if constexpr (MODE <= 1) {
-        if (variant == 0) return launch_batch_v<KIND, MODE, 0, 8, 4>(items, n_items, counter, grid, per_sm, s);
-        if (variant == 3) return launch_batch_v<KIND, MODE, 1, 8, 4>(items, n_items, counter, grid, per_sm, s);
+        if (variant == 0) return launch_batch_v<KIND, MODE, 0, 8, 4, false, BLUE>(items, n_items, counter, grid, per_sm, s);
+        if (variant == 3) return launch_batch_v<KIND, MODE, 1, 8, 4, false, BLUE>(items, n_items, counter, grid, per_sm, s);
         return cudaErrorInvalidValue;
     } else {
         switch (variant) {
-        case 0: return launch_batch_v<KIND, MODE, 0, 8, 4>(items, n_items, counter, grid, per_sm, s);
-        case 1: return launch_batch_v<KIND, MODE, 0, 4, 8>(items, n_items, counter, grid, per_sm, s);
-        case 2: return launch_batch_v<KIND, MODE, 0, 16, 2>(items, n_items, counter, grid, per_sm, s);
-        case 3: return launch_batch_v<KIND, MODE, 1, 8, 4>(items, n_items, counter, grid, per_sm, s);
-        case 4: return launch_batch_v<KIND, MODE, 1, 4, 8>(items, n_items, counter, grid, per_sm, s);
-        case 5: return launch_batch_v<KIND, MODE, 1, 16, 2>(items, n_items, counter, grid, per_sm, s);
-        case 6: return launch_batch_v<KIND, MODE, 0, 8, 4, true>(items, n_items, counter, grid, per_sm, s);
-        case 7: return launch_batch_v<KIND, MODE, 0, 4, 8, true>(items, n_items, counter, grid, per_sm, s);
-        case 8: return launch_batch_v<KIND, MODE, 0, 16, 2, true>(items, n_items, counter, grid, per_sm, s);
+        case 0: return launch_batch_v<KIND, MODE, 0, 8, 4, false, BLUE>(items, n_items, counter, grid, per_sm, s);
+        case 1: return launch_batch_v<KIND, MODE, 0, 4, 8, false, BLUE>(items, n_items, counter, grid, per_sm, s);
+        case 2: return launch_batch_v<KIND, MODE, 0, 16, 2, false, BLUE>(items, n_items, counter, grid, per_sm, s);
+        case 3: return launch_batch_v<KIND, MODE, 1, 8, 4, false, BLUE>(items, n_items, counter, grid, per_sm, s);
+        case 4: return launch_batch_v<KIND, MODE, 1, 4, 8, false, BLUE>(items, n_items, counter, grid, per_sm, s);
+        case 5: return launch_batch_v<KIND, MODE, 1, 16, 2, false, BLUE>(items, n_items, counter, grid, per_sm, s);
+        case 6: return launch_batch_v<KIND, MODE, 0, 8, 4, true, BLUE>(items, n_items, counter, grid, per_sm, s);
+        case 7: return launch_batch_v<KIND, MODE, 0, 4, 8, true, BLUE>(items, n_items, counter, grid, per_sm, s);
+        case 8: return launch_batch_v<KIND, MODE, 0, 16, 2, true, BLUE>(items, n_items, counter, grid, per_sm, s);
         }
         return cudaErrorInvalidValue;
     }
 }
 
-template <int KIND>
+template <int KIND, bool BLUE>
 cudaError_t launch_batch_kind(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant,
                               int* per_sm, cudaStream_t s)
 {
     switch (mode & kModeBase) {  // the exact flag is in the variant
-    case 0: return launch_batch_mode<KIND, 0>(items, n_items, counter, grid, variant, per_sm, s);
-    case 1: return launch_batch_mode<KIND, 1>(items, n_items, counter, grid, variant, per_sm, s);
-    case 2: return launch_batch_mode<KIND, 2>(items, n_items, counter, grid, variant, per_sm, s);
-    case 3: return launch_batch_mode<KIND, 3>(items, n_items, counter, grid, variant, per_sm, s);
-    case 4: return launch_batch_mode<KIND, 4>(items, n_items, counter, grid, variant, per_sm, s);
-    case 5: return launch_batch_mode<KIND, 5>(items, n_items, counter, grid, variant, per_sm, s);
-    case 6: return launch_batch_mode<KIND, 6>(items, n_items, counter, grid, variant, per_sm, s);
+    case 0: return launch_batch_mode<KIND, 0, BLUE && 0 != 0>(items, n_items, counter, grid, variant, per_sm, s);
+    case 1: return launch_batch_mode<KIND, 1, BLUE && 1 != 0>(items, n_items, counter, grid, variant, per_sm, s);
+    case 2: return launch_batch_mode<KIND, 2, BLUE && 2 != 0>(items, n_items, counter, grid, variant, per_sm, s);
+    case 3: return launch_batch_mode<KIND, 3, BLUE && 3 != 0>(items, n_items, counter, grid, variant, per_sm, s);
+    case 4: return launch_batch_mode<KIND, 4, BLUE && 4 != 0>(items, n_items, counter, grid, variant, per_sm, s);
+    case 5: return launch_batch_mode<KIND, 5, BLUE && 5 != 0>(items, n_items, counter, grid, variant, per_sm, s);
+    case 6: return launch_batch_mode<KIND, 6, BLUE && 6 != 0>(items, n_items, counter, grid, variant, per_sm, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -264,15 +264,43 @@ static cudaError_t set_batch_views(const DevView* views, int n_views, cudaStream
 
 }  // namespace stf
 
+// A kind's entry points: NAME renders one view, NAME##_batch runs a batch variant, and
+// NAME##_batch_views fills this module's view constants. Blue-noise modes run kernels compiled in
+// the kind's second translation unit (STF_INSTANTIATE_KIND_BLUE, the same entry points with the
+// suffix _b and its own constant bank), so that the plain kernels carry no trace of them.
 #define STF_INSTANTIATE_KIND(KIND, NAME)                                                        \
     namespace stf {                                                                             \
-    cudaError_t NAME(const DevView& v, int mode, cudaStream_t s) { return launch_view_kind<KIND>(v, mode, s); } \
+    cudaError_t NAME##_b(const DevView& v, int mode, cudaStream_t s);                           \
+    cudaError_t NAME##_b_batch(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant, \
+                               int* per_sm, cudaStream_t s);                                    \
+    cudaError_t NAME##_b_batch_views(const DevView* views, int n_views, cudaStream_t s);        \
+    cudaError_t NAME(const DevView& v, int mode, cudaStream_t s)                                \
+    {                                                                                           \
+        if (mode & kModeFlagBlue) return NAME##_b(v, mode, s);                                  \
+        return launch_view_kind<KIND, false>(v, mode, s);                                       \
+    }                                                                                           \
     cudaError_t NAME##_batch(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant, \
                              int* per_sm, cudaStream_t s)                                       \
     {                                                                                           \
-        return launch_batch_kind<KIND>(items, n_items, counter, grid, mode, variant, per_sm, s); \
+        if (mode & kModeFlagBlue) return NAME##_b_batch(items, n_items, counter, grid, mode, variant, per_sm, s); \
+        return launch_batch_kind<KIND, false>(items, n_items, counter, grid, mode, variant, per_sm, s); \
     }                                                                                           \
-    cudaError_t NAME##_batch_views(const DevView* views, int n_views, cudaStream_t s)           \
+    cudaError_t NAME##_batch_views(const DevView* views, int n_views, int mode, cudaStream_t s) \
+    {                                                                                           \
+        if (mode & kModeFlagBlue) return NAME##_b_batch_views(views, n_views, s);               \
+        return set_batch_views(views, n_views, s);                                              \
+    }                                                                                           \
+    }
+
+#define STF_INSTANTIATE_KIND_BLUE(KIND, NAME)                                                   \
+    namespace stf {                                                                             \
+    cudaError_t NAME##_b(const DevView& v, int mode, cudaStream_t s) { return launch_view_kind<KIND, true>(v, mode, s); } \
+    cudaError_t NAME##_b_batch(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant, \
+                               int* per_sm, cudaStream_t s)                                     \
+    {                                                                                           \
+        return launch_batch_kind<KIND, true>(items, n_items, counter, grid, mode, variant, per_sm, s); \
+    }                                                                                           \
+    cudaError_t NAME##_b_batch_views(const DevView* views, int n_views, cudaStream_t s)         \
     {                                                                                           \
         return set_batch_views(views, n_views, s);                                              \
     }                                                                                           \

@@ -26,7 +26,7 @@ constexpr int kNnWtabFloats = kNnClientWarps * 32 * 8;
 // The client side of one block. VIEWS maps a view index to its constants (a kernel parameter or
 // the batch's constant bank). Every client thread calls round() for the same rounds. EX: exact
 // filtering (bilinear sharing modes).
-template <int F, int MODE, int TW, int TH, bool EX, class VIEWS>
+template <int F, int MODE, int TW, int TH, bool EX, bool BLUE, class VIEWS>
 struct NnRenderClient {
     static constexpr int NT = MODE == 0 ? Taps<F>::N * Taps<F>::N : 1;  // rounds per tile group
     NnPipeSmem& sm;
@@ -69,7 +69,7 @@ struct NnRenderClient {
             } else {
                 // one texel drawn from the pixel's filter PMF (Section 2.2, Section S1)
                 float ux, uy;
-                pixel_uniforms(v, x, y, ux, uy);
+                pixel_uniforms<BLUE>(v, x, y, ux, uy);
                 Axis<F> ax, ay;
                 axis_select<F>(cx, ux, ax);
                 axis_select<F>(cy, uy, ay);
@@ -237,7 +237,7 @@ struct NnParamView {
 };
 
 // One view: persistent blocks walk the view's tile groups (kNnClientWarps tiles of one tile row).
-template <int F, int MODE, int TW, int TH, bool EX = false>
+template <int F, int MODE, int TW, int TH, bool EX = false, bool BLUE = false>
 __global__ void __launch_bounds__(kNnPipeThreads, 2) k_render_neural(const __grid_constant__ DevView v)
 {
     extern __shared__ __align__(128) unsigned char dyn[];
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2) k_render_neural(const __gri
         nn_decode_role(sm, v.flags);
     } else {
         const int warp = threadIdx.x >> 5;
-        NnRenderClient<F, MODE, TW, TH, EX, NnParamView> cl(sm, wtabs + warp * 256, NnParamView{&v}, v.flags);
+        NnRenderClient<F, MODE, TW, TH, EX, BLUE, NnParamView> cl(sm, wtabs + warp * 256, NnParamView{&v}, v.flags);
         const int gx = (v.tiles_x + kNnClientWarps - 1) / kNnClientWarps;
         const int groups = gx * v.tiles_y;
 #pragma unroll 1

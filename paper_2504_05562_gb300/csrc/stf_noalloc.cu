@@ -29,7 +29,7 @@ namespace stf {
 #define STF_DECLARE_BATCH_NA(NAME)                                                                           \
     cudaError_t NAME##_batch(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant, \
                              int* per_sm, cudaStream_t s);                                                     \
-    cudaError_t NAME##_batch_views(const DevView* views, int n_views, cudaStream_t s);
+    cudaError_t NAME##_batch_views(const DevView* views, int n_views, int mode, cudaStream_t s);
 STF_DECLARE_BATCH_NA(launch_view_F32x4)
 STF_DECLARE_BATCH_NA(launch_view_F32x8)
 STF_DECLARE_BATCH_NA(launch_view_F16x4)
@@ -79,9 +79,9 @@ cudaError_t launch_batch_na(int kind, const WorkItem* items, int n_items, int* c
     STF_KIND_SWITCH_NA(batch(items, n_items, counter, grid, mode, variant, per_sm, s))
 }
 
-cudaError_t set_views_na(int kind, const DevView* views, int n_views, cudaStream_t s)
+cudaError_t set_views_na(int kind, const DevView* views, int n_views, int mode, cudaStream_t s)
 {
-    STF_KIND_SWITCH_NA(batch_views(views, n_views, s))
+    STF_KIND_SWITCH_NA(batch_views(views, n_views, mode, s))
 }
 
 // Once per device, with that device current: the scratch's device address and its UNORM8 table.
@@ -216,7 +216,7 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
     for (int k = 0; k < K_COUNT; ++k) {
         const int nvk = group_start[k + 1] - group_start[k];
         if (nvk == 0) continue;
-        e = set_views_na(k, dev->views + group_start[k], nvk, s);
+        e = set_views_na(k, dev->views + group_start[k], nvk, reuse_mode, s);
         if (e != cudaSuccess) return stf_cuda_fail(e, "no-alloc view upload");
         for (int var = 0; var < kVariants; ++var) {
             const int nitems = sub_start[k][var + 1] - sub_start[k][var];

@@ -26,7 +26,7 @@ namespace stf {
 #define STF_DECLARE_BATCH(NAME)                                                                              \
     cudaError_t NAME##_batch(const WorkItem* items, int n_items, int* counter, int grid, int mode, int variant, \
                              int* per_sm, cudaStream_t s);                                                     \
-    cudaError_t NAME##_batch_views(const DevView* views, int n_views, cudaStream_t s);
+    cudaError_t NAME##_batch_views(const DevView* views, int n_views, int mode, cudaStream_t s);
 STF_DECLARE_BATCH(launch_view_F32x4)
 STF_DECLARE_BATCH(launch_view_F32x8)
 STF_DECLARE_BATCH(launch_view_F16x4)
@@ -58,9 +58,11 @@ cudaError_t launch_batch(int kind, const WorkItem* items, int n_items, int* coun
     STF_KIND_SWITCH(batch(items, n_items, counter, grid, mode, variant, per_sm, s))
 }
 
-cudaError_t set_views(int kind, const DevView* views, int n_views, cudaStream_t s)
+// The batch's view constants into the constant bank of the module whose kernels will run (mode
+// selects the kind's blue-noise module or the plain one).
+cudaError_t set_views(int kind, const DevView* views, int n_views, int mode, cudaStream_t s)
 {
-    STF_KIND_SWITCH(batch_views(views, n_views, s))
+    STF_KIND_SWITCH(batch_views(views, n_views, mode, s))
 }
 
 // ------------------------------------------------------------------------------ view classes
@@ -319,7 +321,7 @@ stf_status render_batch_impl(const stf_view* views, int n, int filter, int mode,
         if (r == cudaSuccess) r = cudaMemsetAsync(b.counters[k], 0, ncounters * sizeof(int), s);
         for (size_t gi = 0; gi < groups.size() && r == cudaSuccess; ++gi) {
             const Group& g = groups[gi];
-            r = set_views(g.kind, reinterpret_cast<const DevView*>(b.dev[k] + g.views_off), (int)g.views.size(), s);
+            r = set_views(g.kind, reinterpret_cast<const DevView*>(b.dev[k] + g.views_off), (int)g.views.size(), mode, s);
             if (r == cudaSuccess) r = cudaEventRecord(b.fork, s);
             for (size_t j = 0; j < g.subs.size() && r == cudaSuccess; ++j) {
                 const Sub& sub = g.subs[j];
