@@ -112,10 +112,17 @@ def algorithmic_bytes(a):
     return out + vis * REC_BYTES[a.fmt]
 
 
-def src_hash():
+# the sources whose code a kernel's DRAM traffic depends on (its body, helpers and launch)
+TRAFFIC_SOURCES = {
+    "k_render_view": ["stf_device.cuh", "stf_kernels.cuh", "stf_launch.cuh"],
+    "k_render_neural": ["stf_device.cuh", "stf_kernels.cuh", "stf_launch.cuh", "stf_neural.cuh", "stf_nn_render.cuh"],
+}
+
+
+def src_hash(kernel="k_render_view"):
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2504_05562_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in TRAFFIC_SOURCES[kernel]:
+        h.update(open(os.path.join(ROOT, "paper_2504_05562_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -219,7 +226,7 @@ def load_traffic(kernel_key):
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         e = t.get(kernel_key)
-        if e and e.get("src_hash") == src_hash():
+        if e and e.get("src_hash") == src_hash(kernel_key.split("/")[0]):
             return e["dram_bytes_per_launch"]
     except Exception:
         pass

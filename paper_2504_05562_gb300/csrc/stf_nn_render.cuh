@@ -48,6 +48,9 @@ struct NnRenderClient {
     __device__ __forceinline__ void produce(int view, bool active, int tx, int ty, int t, int slot)
     {
         const int row = warp * 32 + lane;
+        // the slot's previous round (r - 2) may still be read by other lanes of this warp, whose
+        // sharing loops read every lane's record and decoded texel: wait for all of them
+        __syncwarp();
         if (active) {
             const DevView& v = views(view);
             const int x = tx * TW + lane % TW, y = ty * TH + lane / TW;

@@ -153,3 +153,67 @@ def test_checkpoint_resume_is_bit_exact(tmp_path):
     c.train(tex, 20)
     Lc, Pc = c.get_params()
     assert np.array_equal(La, Lc) and np.array_equal(Pa, Pc)
+
+
+def _exact_decoder(neural, tex=128, lat=32, seed=11):
+    """A decoder whose inference is exact on both sides: latents in (1/8)Z, sparse weights in
+    (1/8)Z (8 nonzeros per row, the 8 position features unused), biases in (1/64)Z. Every
+    interpolated input lies in (1/512)Z, every FP32 sum of the three layers needs at most 24
+    significant bits, and the FP16 roundings of exact values are the same on both sides, so the
+    GPU's decode equals the oracle's emulation bit for bit whatever the summation order."""
+    dec = neural.Decoder(tex, tex, lat, lat, batch=1024, seed=seed)
+    rng = np.random.default_rng(seed)
+    L = rng.integers(-8, 9, (lat, lat, 16)).astype(np.float32) / 8.0
+
+    def sparse(rows, cols, used):
+        W = np.zeros((rows, cols), np.float32)
+        for r in range(rows):
+            k = rng.choice(used, 8, replace=False)
+            W[r, k] = rng.choice([-1.0, 1.0], 8) / 8.0
+        return W
+
+    W1, W2, W3 = sparse(64, 24, 16), sparse(64, 64, 64), sparse(8, 64, 64)
+    b1, b2, b3 = (rng.integers(-16, 17, n).astype(np.float32) / 64.0 for n in (64, 64, 8))
+    P = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3]).astype(np.float32)
+    dec.set_params(L, P)
+    return dec, L, P
+
+
+def test_exact_decoder_is_bit_exact():
+    stf, neural = _mods()
+    dec, L, P = _exact_decoder(neural)
+    idx = _all_texels(128, 128)
+    out = dec.decode(torch.from_numpy(idx).cuda()).cpu().numpy()
+    lat16, w16, b32 = O.nn_pack_inference(L, P)
+    ref = O.nn_decode_f32(lat16, 4, w16, b32, idx)
+    assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("filt,mode", [(0, O.QUAD2), (0, O.WAVE2), (0, O.WAVE3), (0, O.WAVE4), (1, O.WAVE3),
+                                       (1, O.WAVE4), (0, O.FULL), (1, O.FULL), (0, O.ONE_TAP),
+                                       (0, O.WAVE4 | O.FLAG_EXACT), (0, O.SPARSE9)])
+def test_render_neural_material_tight(filt, mode):
+    """With exactly decodable texels, a neural render matches the oracle within the colour bar of
+    the stored kinds (no allowance for decode roundings): sharing, exact filtering and sparse
+    footprints over the decode pipeline, on a frame of many rounds."""
+    stf, neural = _mods()
+    dec, L, P = _exact_decoder(neural)
+    tex = dec.texture()
+    lat16, w16, b32 = O.nn_pack_inference(L, P)
+    mat = O.neural_material(128, 128, lat16, 4, w16, b32)
+    view = W.screen_aligned_view(256, 128, 128, 128, 2.7, filt, origin=(9.3, 17.1))
+    extra = {}
+    if (mode & 15) == O.SPARSE9:
+        rng = np.random.default_rng(4)
+        tab = np.array([[[lane] + list(rng.permutation([j for j in range(32) if j != lane])[:8]) for lane in range(32)]
+                        for _ in range(2)], np.int8)
+        stf.set_sparse_footprints(tab, (8, 4))
+        extra["footprints"] = tab
+    out, idx, ch = stf.render(tex, view, mode, seed=3, debug=True)
+    torch.cuda.synchronize()
+    stf.sync()
+    r_out, r_idx, r_ch = O.render(mat, dict(view, **extra), mode, seed=3, want_channels=True)
+    if (mode & 15) != O.FULL:
+        assert np.array_equal(idx.cpu().numpy().view(np.uint32), r_idx)
+    g, r = ch.cpu().numpy().astype(np.float64), r_ch.astype(np.float64)
+    assert np.all(np.abs(g - r) <= 1e-5 * np.maximum(np.abs(r), 1.0)), float(np.abs(g - r).max())
