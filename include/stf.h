@@ -196,7 +196,10 @@ stf_status stf_render_views(const stf_view* views, int n, int filter, int reuse_
  * to the device in one copy from a pinned staging buffer; copy, counter reset and kernels are
  * captured once into a CUDA graph and replayed while the batch keeps its shape (same views per
  * kind, same item count). */
-enum { STF_OPT_BATCH_GRAPHS = 1 };                          /* 1 (default): replay CUDA graphs */
+enum { STF_OPT_BATCH_GRAPHS = 1,   /* 1 (default): replay CUDA graphs */
+       STF_OPT_PIPELINE_BLOCKS = 2 /* > 0: at most this many persistent blocks for a neural-material
+                                    * view (each then runs more decode rounds); 0 (default): fill the
+                                    * SMs */ };
 enum { STF_STAT_GRAPH_BUILDS = 1, STF_STAT_GRAPH_REPLAYS = 2 };
 stf_status stf_set_option(int option, long long value);
 stf_status stf_get_stat(int stat, long long* value);

@@ -42,6 +42,9 @@ bool stf_sparse_state(const uint8_t** table, int* patterns, int* tile_w, int* ti
 // The current device's blue-noise masks (stf_set_blue_noise); false if none.
 bool stf_blue_state(const uint16_t** ranks, int* shift);
 
+// STF_OPT_PIPELINE_BLOCKS (0: fill the SMs).
+extern int g_pipeline_blocks;
+
 // resident blocks per SM, counted from the kernel's resources (stf_api.cu)
 cudaError_t stf_resident_blocks(const void* kernel, int threads, int dyn_bytes, int* n);
 

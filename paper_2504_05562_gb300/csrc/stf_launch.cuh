@@ -49,7 +49,9 @@ static cudaError_t launch_one(const DevView& v, cudaStream_t s)
         cudaError_t e = prepare_dynamic(k_render_neural<F, MODE, TW, TH, EX, BLUE>, dyn, kNnPipeThreads, cached, &per_sm);
         if (e != cudaSuccess) return e;
         const long long groups = (long long)((v.tiles_x + kNnClientWarps - 1) / kNnClientWarps) * v.tiles_y;
-        const unsigned blocks = (unsigned)(groups < (long long)per_sm * device_sms() ? groups : (long long)per_sm * device_sms());
+        long long cap = (long long)per_sm * device_sms();
+        if (g_pipeline_blocks > 0 && g_pipeline_blocks < cap) cap = g_pipeline_blocks;
+        const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
         k_render_neural<F, MODE, TW, TH, EX, BLUE><<<blocks, kNnPipeThreads, dyn, s>>>(v);
     } else {
         k_render_view<KIND, F, MODE, TW, TH, EX, ALT, BLUE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);

@@ -246,8 +246,8 @@ __device__ __forceinline__ uint32_t nn_chunk(int m, int j, int K) { return (m >>
 //      TMEM); between layers the epilogue warpgroup turns a tile's accumulators into FP16
 //      activations (ReLU) in TMEM, the A operand of the next layer, and arrives on epi[tile]; the
 //      tiles alternate, so one tile's products overlap the other's epilogue;
-//   3. the epilogue warpgroup writes the 8 FP32 outputs of each row over the consumed layer-1
-//      operand and arrives on out_full[slot]; the client threads read their rows back (and, when
+//   3. the epilogue warpgroup writes the 8 FP32 outputs of each row over that row's consumed
+//      layer-1 inputs and arrives on out_full[slot]; the client threads read their rows back (and, when
 //      sharing, their warp's other rows).
 // Two slots let the clients prepare round r + 1 while round r is decoded. Every wait is bounded:
 // one that gives up counts itself in flags[0], and all later waits of the launch return at once
@@ -258,7 +258,7 @@ constexpr int kNnClients = kNnClientWarps * 32;    // 256 texels per round
 constexpr int kNnMmaWarp = 8;
 constexpr int kNnRows = 256;                       // operand rows per round (two M = 128 tiles)
 constexpr int kNnPipeThreads = 416;
-constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: layer-1 operand, then 256 x 8 FP32 outputs
+constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: layer-1 operand, then each row's 8 FP32 outputs
 // TMEM columns of a block: FP32 accumulators of the two tiles at 0 and 64 (64 columns each), and
 // the tiles' FP16 hidden activations (the A operand of layers 2 and 3, two K elements per
 // 32-bit column, K = 80 -> 40 columns) at 128 and 168.
@@ -391,11 +391,16 @@ __device__ __forceinline__ void nn_stage_inputs(const NnPipeSmem& sm, int client
     nn_features(nd, x, y, row);
 }
 
+// The decoded outputs of row `row` sit in the row's own layer-1 chunks 0 and 1 (16 bytes each):
+// a row's outputs overwrite only its own inputs, so a client warp writing the next round's rows
+// of this slot never touches another warp's outputs (and 8 lanes read 8 distinct bank groups).
+__device__ __forceinline__ uint32_t nn_out_offset(int row, int half) { return nn_chunk(row, half, kNnK1); }
+
 // The 8 decoded FP32 channels of row `row` (valid after out_full of its round).
 __device__ __forceinline__ void nn_get_outputs(const NnPipeSmem& sm, int slot, int row, float (&t)[8])
 {
-    const float4* o = reinterpret_cast<const float4*>(sm.io[slot] + row * 32);
-    const float4 a = o[0], b = o[1];
+    const float4 a = *reinterpret_cast<const float4*>(sm.io[slot] + nn_out_offset(row, 0));
+    const float4 b = *reinterpret_cast<const float4*>(sm.io[slot] + nn_out_offset(row, 1));
     t[0] = a.x; t[1] = a.y; t[2] = a.z; t[3] = a.w;
     t[4] = b.x; t[5] = b.y; t[6] = b.z; t[7] = b.w;
 }
@@ -583,9 +588,8 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
             tile_wait(mt);
             float o[8];
             tmem_ld8(t_lane + mt * 64, o);
-            float4* dst = reinterpret_cast<float4*>(sm.io[slot] + (mt * 128 + m) * 32);
-            dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-            dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+            *reinterpret_cast<float4*>(sm.io[slot] + nn_out_offset(mt * 128 + m, 0)) = make_float4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<float4*>(sm.io[slot] + nn_out_offset(mt * 128 + m, 1)) = make_float4(o[4], o[5], o[6], o[7]);
         }
         tc_fence_before();
         nn_arrive(smem_u32(&sm.out_full[slot]));
