@@ -278,6 +278,15 @@ stf_status stf_blue_noise_masks(int size, double sigma, int quad_energy, unsigne
  * Errors: STF_ERR_INVALID_ARG (nothing changes). */
 stf_status stf_set_blue_noise(const uint16_t* ranks, int size);
 
+/* Replaces a texture's texels (no allocation): `data` holds plane 0 exactly as at creation
+ * (width * height records of the plane's format and channels), host or device memory
+ * (data_on_device). For textures kept in their plane's own layout (one plane: FP32 x 4 or 8,
+ * FP16 x 4 or 8, BF16 x 8, E4M3 x 8 whose scales stay); others STF_ERR_UNSUPPORTED. One
+ * cudaMemcpyAsync on the library stream, ordered with renders there: host data must stay valid
+ * until the stream reaches the copy, and must be pinned for the copy to be asynchronous. This
+ * is how a frame loop streams new texel data (e.g. a video or procedural texture) each frame. */
+stf_status stf_update_texture(stf_texture* tex, const void* data, int data_on_device);
+
 /* Frees a texture (NULL is a no-op). The caller ensures no enqueued work still reads it. */
 stf_status stf_destroy(stf_texture* tex);
 

@@ -300,6 +300,27 @@ static stf_status to_device(const void* src, size_t bytes, int on_device, DevBuf
     return STF_OK;
 }
 
+extern "C" stf_status stf_update_texture(stf_texture* t, const void* data, int data_on_device)
+{
+    if (!t || !data) return stf_fail(STF_ERR_INVALID_ARG, "stf_update_texture: null argument");
+    size_t rec = 0;
+    switch (t->kind) {
+    case K_F32x4: rec = 16; break;
+    case K_F32x8: rec = 32; break;
+    case K_F16x4: rec = 8; break;
+    case K_F16x8: case K_BF16x8: rec = 16; break;
+    case K_E4M3x8: rec = 8; break;
+    default:
+        return stf_fail(STF_ERR_UNSUPPORTED, "stf_update_texture: the texture's texels are not its plane's bytes "
+                                             "(interleaved, widened or neural): create a new texture");
+    }
+    if (t->widened) return stf_fail(STF_ERR_UNSUPPORTED, "stf_update_texture: the texture was widened at creation");
+    const size_t bytes = (size_t)t->width * t->height * rec;
+    const cudaError_t e = cudaMemcpyAsync(t->texels, data, bytes, data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                          stf_stream());
+    return e == cudaSuccess ? STF_OK : stf_cuda_fail(e, "stf_update_texture copy");
+}
+
 extern "C" stf_status stf_create_texture(const stf_texture_desc* d, stf_texture** out)
 {
     if (!d || !out) return stf_fail(STF_ERR_INVALID_ARG, "stf_create_texture: null argument");
@@ -384,6 +405,7 @@ extern "C" stf_status stf_create_texture(const stf_texture_desc* d, stf_texture*
     } else {
         // widen to FP32 records of 4 or 8 channels
         kind = C <= 4 ? K_F32x4 : K_F32x8;
+        t->widened = true;
         const int oc = C <= 4 ? 4 : 8;
         DevBuf stage[4], sdev;
         PlaneDesc pd;

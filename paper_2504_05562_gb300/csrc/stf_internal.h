@@ -16,6 +16,7 @@ struct stf_texture {
     int scale_shift, scale_tiles_x;
     const stf_decoder* decoder;     // NEURAL kind
     const void* decoder_params;     // device parameter block of the decoder (NEURAL kind)
+    bool widened = false;           // texels converted at creation (no plane-byte updates)
 };
 
 stf_status stf_fail(stf_status s, const char* fmt, ...);

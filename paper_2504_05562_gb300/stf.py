@@ -59,7 +59,7 @@ EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_str
            "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy", "stf_set_option", "stf_get_stat",
            "stf_autotune", "stf_view_config", "stf_autotune_save", "stf_autotune_load", "stf_autotune_clear",
            "stf_render_views_noalloc", "stf_sparse_footprints", "stf_set_sparse_footprints",
-           "stf_blue_noise_masks", "stf_set_blue_noise")
+           "stf_blue_noise_masks", "stf_set_blue_noise", "stf_update_texture")
 NOALLOC_MAX_VIEWS, NOALLOC_MAX_ITEMS = 224, 262144
 OPT_BATCH_GRAPHS, OPT_PIPELINE_BLOCKS = 1, 2
 STAT_GRAPH_BUILDS, STAT_GRAPH_REPLAYS = 1, 2
@@ -105,6 +105,7 @@ def _bind_extra(L):
     L.stf_set_sparse_footprints.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
     L.stf_blue_noise_masks.argtypes = [C.c_int, C.c_double, C.c_int, C.c_ulonglong, C.c_void_p]
     L.stf_set_blue_noise.argtypes = [C.c_void_p, C.c_int]
+    L.stf_update_texture.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
     L.stf_sparse_footprints.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int,
                                         C.c_ulonglong, C.c_int, C.c_void_p, C.c_void_p]
     for n in ("stf_set_option", "stf_get_stat", "stf_autotune", "stf_view_config", "stf_autotune_save",
@@ -172,6 +173,13 @@ class Texture:
         self.handle = h.value
         self.width, self.height = d.width, d.height
         del keep
+
+    def update(self, data, on_device=False):
+        """Replaces the texels with plane 0 bytes laid out as at creation: a CUDA tensor
+        (on_device) or a host buffer (numpy array or CPU tensor; pin it for an asynchronous copy).
+        The caller keeps `data` alive until the library stream has run the copy."""
+        ptr = data.data_ptr() if hasattr(data, "data_ptr") else data.ctypes.data
+        _check(load().stf_update_texture(self.handle, ptr, 1 if on_device else 0))
 
     def close(self):
         if getattr(self, "handle", None):

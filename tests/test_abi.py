@@ -51,6 +51,7 @@ def test_invalid_arguments_rejected_on_host():
         assert "exact filtering" in stf.last_error()
     assert L.stf_render_views(arr, 1, 0, 9 | stf.MODE_FLAG_EXACT, 0) == stf.ERR_INVALID_ARG
     assert L.stf_create_texture(None, None) == stf.ERR_INVALID_ARG
+    assert L.stf_update_texture(None, None, 0) == stf.ERR_INVALID_ARG
     d = stf.TextureDesc()
     d.width, d.height, d.num_planes = 0, 4, 1
     h = C.c_void_p()

@@ -189,3 +189,25 @@ def test_full_size_config3_fp16_frame(filt):
     mat = W.material_c3(W.FP16)
     v = W.config3_view(filt, frame=1)
     run_both(mat, v, O.WAVE3, seed=0)
+
+
+def test_update_texture_equals_new_texture():
+    """stf_update_texture replaces the texels in place: rendering after an update from host (pinned
+    or not) or device data equals rendering a texture created from the new data."""
+    stf = _stf()
+    a = W.material_c3(W.FP16, size=256, seed=1)
+    b = W.material_c3(W.FP16, size=256, seed=2)
+    view = W.with_shading(W.screen_aligned_view(96, 64, 256, 256, 3.0, 0, origin=(5.5, 9.5)), "c3")
+    tex = stf.Texture(a)
+    fresh = stf.Texture(b)
+    want, _, _ = stf.render(fresh, view, stf.MODE_WAVE3, seed=2)
+    raw = np.ascontiguousarray(b["planes"][0][2]).view(np.uint8).reshape(-1)
+    for src, dev in ((raw, False), (torch.from_numpy(raw).pin_memory(), False), (torch.from_numpy(raw).cuda(), True)):
+        tex.update(np.ascontiguousarray(a["planes"][0][2]))  # back to the old texels first
+        tex.update(src, on_device=dev)
+        got, _, _ = stf.render(tex, view, stf.MODE_WAVE3, seed=2)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want)
+    widened = stf.Texture(W.material_c2(size=64))
+    with pytest.raises(stf.StfError, match="create a new texture"):
+        widened.update(np.zeros(64 * 64 * 8, np.uint8))
