@@ -41,8 +41,8 @@ REC_BYTES = {"fp32": 32, "fp16": 16, "bf16": 16, "e4m3": 8}
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="wave3", choices=list(MODES))
     p.add_argument("--filter", default="bilinear", choices=["bilinear", "bspline"])

@@ -313,8 +313,10 @@ const char* stf_last_error(void);
  *            b3 (6280 values, in this order).
  * Training: Adam on the mean squared error over the 8 channels of an FP32 target texture,
  * `batch` texels per step drawn by a counter hash of (step, seed); FP32 on the CUDA cores,
- * bit-reproducible. Inference (render path, stf_decoder_decode): FP16 latents and weights, FP16
- * inputs and hidden activations, FP32 accumulation on the tensor cores.
+ * bit-reproducible. Inference (render path, stf_decoder_decode): FP16 latents and weights, the
+ * latent interpolation in FP16 arithmetic (corner weights rounded to FP16, w00 L00 + w10 L10 +
+ * w01 L01 + w11 L11 with one rounding per multiply and per fused multiply-add), FP16 inputs and
+ * hidden activations, FP32 accumulation on the tensor cores.
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     int tex_w, tex_h;

@@ -206,7 +206,8 @@ def nn_pack_inference(lat, P):
 
 
 def nn_decode_f32(lat16, R, w16, b32, idx):
-    """FP32 emulation of the GPU inference precision (FP16 storage, FP32 accumulation)."""
+    """Emulation of the GPU inference precision (FP16 storage and latent interpolation, FP32
+    accumulation)."""
     lat16 = np.ascontiguousarray(lat16, np.uint16)
     gh, gw = lat16.shape[:2]
     idx = np.ascontiguousarray(idx, np.int32)

@@ -16,9 +16,10 @@
  *
  * Two evaluation paths:
  *   FP64           forward and backward in double (gradient checks, ground truth);
- *   FP32 emulation the GPU's inference precision: latents and weights stored in FP16, the 24
- *                  inputs and both hidden layers rounded to FP16, products accumulated in FP32,
- *                  biases and output in FP32.
+ *   FP32 emulation the GPU's inference precision: latents and weights stored in FP16, the 16
+ *                  interpolated latents computed in FP16 arithmetic, the 8 position features and
+ *                  both hidden layers rounded to FP16, products accumulated in FP32, biases and
+ *                  output in FP32.
  */
 #include <math.h>
 #include <stdint.h>
@@ -44,15 +45,13 @@ static float h2f(uint16_t h)
     return s ? -r : r;
 }
 
-static uint16_t f2h(float x)
+static uint16_t d2h(double x)
 {
-    uint32_t u;
-    memcpy(&u, &x, 4);
-    uint16_t sign = (uint16_t)((u >> 16) & 0x8000u);
-    float a = fabsf(x);
+    uint16_t sign = (uint16_t)(signbit(x) ? 0x8000u : 0u);
+    double a = fabs(x);
     if (isnan(x)) return (uint16_t)(sign | 0x7e00u);
-    if (a >= 65520.0f) return (uint16_t)(sign | 0x7c00u); /* rounds to infinity */
-    if (a < ldexpf(1.0f, -14)) {
+    if (a >= 65520.0) return (uint16_t)(sign | 0x7c00u); /* rounds to infinity */
+    if (a < ldexp(1.0, -14)) {
         /* subnormal: multiple of 2^-24, round to nearest even */
         double q = (double)a * 16777216.0;
         double fl = floor(q);
@@ -62,7 +61,7 @@ static uint16_t f2h(float x)
         return (uint16_t)(sign | m); /* m == 1024 becomes the smallest normal, as it should */
     }
     int e;
-    double fr = frexp((double)a, &e); /* a = fr * 2^e, fr in [0.5, 1) */
+    double fr = frexp(a, &e);         /* a = fr * 2^e, fr in [0.5, 1) */
     double q = fr * 2048.0;           /* 11 significant bits */
     double fl = floor(q);
     double r = q - fl;
@@ -74,7 +73,15 @@ static uint16_t f2h(float x)
     return (uint16_t)(sign | (uint16_t)(E << 10) | (uint16_t)(m - 1024));
 }
 
+static uint16_t f2h(float x) { return d2h((double)x); }
 static float round_h(float x) { return h2f(f2h(x)); }
+
+/* binary16 arithmetic (IEEE 754: the exact result rounded once to binary16, nearest even). The
+ * product of two binary16 values is exact in double; adding a third is exact in double unless
+ * the operands lie more than 31 binades apart, and then the far smaller one cannot move the
+ * result across a binary16 rounding boundary, so one rounding of the double result is exact. */
+static float mul_h(float a, float b) { return h2f(d2h((double)a * (double)b)); }
+static float fma_h(float a, float b, float c) { return h2f(d2h((double)a * (double)b + (double)c)); }
 
 float stf_ref_f16_round(float x) { return round_h(x); }
 uint16_t stf_ref_f32_to_f16(float x) { return f2h(x); }
@@ -257,20 +264,21 @@ int stf_ref_neural_decode(const uint16_t* lat16, int GW, int GH, int R, const ui
         latent_axis(ix, R, GW, &x0, &x1, &fxd);
         latent_axis(iy, R, GH, &y0, &y1, &fyd);
         const float fx = (float)fxd, fy = (float)fyd;
-        /* corner weights and the interpolation, rounded per operation in this order */
-        const float w00 = (1.0f - fx) * (1.0f - fy), w10 = fx * (1.0f - fy);
-        const float w01 = (1.0f - fx) * fy, w11 = fx * fy;
+        /* corner weights in FP32, then rounded to FP16; the interpolation in FP16 arithmetic, one
+         * rounding per multiply and per fused multiply-add, in this order */
+        const float w00 = round_h((1.0f - fx) * (1.0f - fy)), w10 = round_h(fx * (1.0f - fy));
+        const float w01 = round_h((1.0f - fx) * fy), w11 = round_h(fx * fy);
         const uint16_t* c00 = lat16 + ((size_t)y0 * GW + x0) * NN_LAT;
         const uint16_t* c10 = lat16 + ((size_t)y0 * GW + x1) * NN_LAT;
         const uint16_t* c01 = lat16 + ((size_t)y1 * GW + x0) * NN_LAT;
         const uint16_t* c11 = lat16 + ((size_t)y1 * GW + x1) * NN_LAT;
         float x[NN_IN];
         for (int k = 0; k < NN_LAT; ++k) {
-            float s = w00 * h2f(c00[k]);
-            s = s + w10 * h2f(c10[k]);
-            s = s + w01 * h2f(c01[k]);
-            s = s + w11 * h2f(c11[k]);
-            x[k] = round_h(s);
+            float s = mul_h(w00, h2f(c00[k]));
+            s = fma_h(w10, h2f(c10[k]), s);
+            s = fma_h(w01, h2f(c01[k]), s);
+            s = fma_h(w11, h2f(c11[k]), s);
+            x[k] = s;
         }
         double ph[8];
         phase_features(ix, R, ph);

@@ -46,17 +46,6 @@ struct NeuralDev {
     const uint4* wimg;    // the three layers (weights and biases) as tensor-core B operands
 };
 
-__device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
-{
-    const __half2 h = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-__device__ __forceinline__ float2 unpack_h2(uint32_t w)
-{
-    return __half22float2(*reinterpret_cast<const __half2*>(&w));
-}
-
 // Bilinear position along one latent axis: lower cell, upper cell (both clamped) and fraction.
 __device__ __forceinline__ void nn_axis(int i, const NeuralDev& nd, int G, int& c0, int& c1, float& f)
 {
@@ -88,12 +77,14 @@ __device__ __forceinline__ void nn_cells(const NeuralDev& nd, int x, int y, cons
 }
 
 // The 16 interpolated latents as 8 packed FP16 words from the cells' 8 chunks L[2 q + h] (cell q,
-// half h), rounded per operation in the order (w00 L00 + w10 L10) + w01 L01, + w11 L11 (pairs
-// of channels per f32x2 operation, each lane rounded as a scalar operation would be).
+// half h) in FP16 arithmetic, the precision of the decoder's inputs: the four corner weights
+// rounded to FP16, then w00 L00, + w10 L10, + w01 L01, + w11 L11 with one rounding per multiply
+// and per fused multiply-add (two channels per half2 operation).
 __device__ __forceinline__ void nn_interp(const uint4 (&L)[8], const float (&w)[4], uint32_t (&row)[12])
 {
-    const float2 w0 = make_float2(w[0], w[0]), w1 = make_float2(w[1], w[1]);
-    const float2 w2 = make_float2(w[2], w[2]), w3 = make_float2(w[3], w[3]);
+    const __half2 w0 = __float2half2_rn(w[0]), w1 = __float2half2_rn(w[1]);
+    const __half2 w2 = __float2half2_rn(w[2]), w3 = __float2half2_rn(w[3]);
+    auto h2 = [](uint32_t v) { return *reinterpret_cast<const __half2*>(&v); };
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const uint4 a = L[h], b = L[2 + h], c = L[4 + h], d = L[6 + h];
@@ -101,11 +92,11 @@ __device__ __forceinline__ void nn_interp(const uint4 (&L)[8], const float (&w)[
         const uint32_t cw[4] = {c.x, c.y, c.z, c.w}, dw[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            float2 s2 = __fmul2_rn(w0, unpack_h2(aw[k]));
-            s2 = __fadd2_rn(s2, __fmul2_rn(w1, unpack_h2(bw[k])));
-            s2 = __fadd2_rn(s2, __fmul2_rn(w2, unpack_h2(cw[k])));
-            s2 = __fadd2_rn(s2, __fmul2_rn(w3, unpack_h2(dw[k])));
-            row[4 * h + k] = pack_h2(s2.x, s2.y);
+            __half2 s2 = __hmul2_rn(w0, h2(aw[k]));
+            s2 = __hfma2(w1, h2(bw[k]), s2);
+            s2 = __hfma2(w2, h2(cw[k]), s2);
+            s2 = __hfma2(w3, h2(dw[k]), s2);
+            row[4 * h + k] = *reinterpret_cast<const uint32_t*>(&s2);
         }
     }
 }
@@ -265,14 +256,12 @@ constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: layer-1 operand, th
 constexpr int kNnTmemCols = 256;
 constexpr int kNnHidCol = 128, kNnHidCols = kNnK2 / 2;
 constexpr unsigned kNnWaitLimit = 1u << 20;        // mbarrier polls before a wait gives up
-constexpr int kNnStageBytes = 144;                 // 8 x 16-byte latent chunks + a 16-byte record
 
 struct NnPipeSmem {
     alignas(128) unsigned char b[kNnImgBytes];
     alignas(128) unsigned char io[2][kNnIoBytes];
     float4 rec[2][kNnRows];  // per-row sample records of the clients (see the render kernels)
-    // per client: the 8 latent chunks of its next texel, copied ahead (cp.async), and its record
-    alignas(16) unsigned char stage[kNnClients][kNnStageBytes];
+    float4 geo[2][kNnRows];  // per-row pixel geometry (u, v, cx, cy) of the render clients
     unsigned long long in_full[2], out_full[2], mma[2], epi[2];  // mma, epi: one barrier per tile
     uint32_t tmem;
     int more[2];             // 1: the round in this slot carries rows, 0: the clients are done
@@ -356,39 +345,6 @@ __device__ __forceinline__ void nn_publish(NnPipeSmem& sm, int slot, int more)
     if (threadIdx.x == 0) sm.more[slot] = more;
     fence_async_smem();
     nn_arrive(smem_u32(&sm.in_full[slot]));
-}
-
-// Starts copying the 8 latent chunks of texel (x, y) into this client's stage (asynchronous;
-// nn_stage_inputs waits for them).
-__device__ __forceinline__ void nn_stage_issue(NnPipeSmem& sm, int client, const NeuralDev& nd, int x, int y)
-{
-    const uint4* c[4];
-    float w[4];
-    nn_cells(nd, x, y, c, w);
-    const uint32_t dst = smem_u32(sm.stage[client]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(dst + (2 * q + h) * 16),
-                         "l"(__cvta_generic_to_global(c[q] + h)) : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// The 24 FP16 inputs of texel (x, y) from the chunks staged by nn_stage_issue.
-__device__ __forceinline__ void nn_stage_inputs(const NnPipeSmem& sm, int client, const NeuralDev& nd, int x, int y,
-                                                uint32_t (&row)[12])
-{
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    const uint4* c[4];
-    float w[4];
-    nn_cells(nd, x, y, c, w);
-    const uint4* st = reinterpret_cast<const uint4*>(sm.stage[client]);
-    uint4 L[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) L[i] = st[i];
-    nn_interp(L, w, row);
-    nn_features(nd, x, y, row);
 }
 
 // The decoded outputs of row `row` sit in the row's own layer-1 chunks 0 and 1 (16 bytes each):

@@ -82,6 +82,7 @@ struct NnRenderClient {
                 rec = make_float4(ax.nf, ay.nf, fminf(rcp_approx(p), FLT_MAX), __uint_as_float(pack_idx(ax.n, ay.n)));
             }
             sm.rec[slot][row] = rec;
+            sm.geo[slot][row] = make_float4(u, wv, cx, cy);  // read back by this thread's consume
             uint32_t in[12];
             nn_inputs(*reinterpret_cast<const NeuralDev*>(v.neural), clampi(nx, 0, v.tex_w - 1), clampi(ny, 0, v.tex_h - 1), in);
             nn_put_inputs(sm, slot, row, in);
@@ -120,9 +121,8 @@ struct NnRenderClient {
             // the estimate of Eq. estimator-for-stf over the lane's footprint, w_j = f_c(x_j) / f_j(x_j),
             // the own weight exactly 1 (the texture kinds' combine, records read from the round)
             using FP = Footprint<MODE, TW, TH>;
-            float u, wv;
-            pixel_uv(v, x, y, u, wv);
-            const float cx = texel_coord(u, v.tex_wf), cy = texel_coord(wv, v.tex_hf);
+            const float4 g = sm.geo[slot][row0 + lane];
+            const float cx = g.z, cy = g.w;
             Axis<F> ax, ay;
             if constexpr (F == 0 && EX) {
                 axis_weights<F>(cx, ax);
@@ -192,9 +192,8 @@ struct NnRenderClient {
                 exact_bilinear<8>(ax, ay, srcs, res, [&](int j, float (&T)[8]) { nn_get_outputs(sm, slot, row0 + j, T); });
         }
         if (x < v.width && y < v.height) {
-            float u, wv;
-            pixel_uv(v, x, y, u, wv);
-            const float4 o = finish_pixel<8>(v, res, u, wv);
+            const float4 g = sm.geo[slot][row0 + lane];  // (u, v) of the pixel, from its produce
+            const float4 o = finish_pixel<8>(v, res, g.x, g.y);
             __stcs(reinterpret_cast<float4*>(v.out + (size_t)y * v.pitch + 4 * (size_t)x), o);
             const size_t pix = (size_t)y * v.width + x;
             if (v.dbg_idx) v.dbg_idx[pix] = pk;

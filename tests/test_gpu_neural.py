@@ -62,11 +62,12 @@ def test_decode_matches_oracle_emulation():
     lat16, w16, b32 = O.nn_pack_inference(L, P)
     ref = O.nn_decode_f32(lat16, 4, w16, b32, idx)
     assert_neural_close(out, ref, "decode")
-    # a non-multiple of 32 texels, and out-of-range coordinates clamp to the edge
+    # a non-multiple of 32 texels, and out-of-range coordinates clamp to the edge: each row of the
+    # products is summed independently of the others, so these decodes equal the same texels'
+    # rows of the full decode bit for bit (the oracle comparison of those rows is the one above)
     idx2 = np.array([5 | (7 << 16), 63 | (63 << 16), 100 | (3 << 16)], np.int32)
     out2 = dec.decode(torch.from_numpy(idx2).cuda()).cpu().numpy()
-    ref2 = O.nn_decode_f32(lat16, 4, w16, b32, np.array([5 | (7 << 16), 63 | (63 << 16), 63 | (3 << 16)], np.int32))
-    assert_neural_close(out2, ref2, "decode tail")
+    assert np.array_equal(out2, out[[7 * 64 + 5, 63 * 64 + 63, 3 * 64 + 63]])
 
 
 def test_gradients_match_oracle():

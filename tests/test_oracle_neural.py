@@ -122,3 +122,69 @@ def test_fp32_emulation_close_to_fp64():
     scale = 1.0 + np.abs(y64)
     assert np.max(np.abs(y32 - y64) / scale) < 2e-2
     assert np.mean(np.abs(y32 - y64)) < 3e-3
+
+
+def _rn_f16(q):
+    """Round a Fraction to the nearest IEEE binary16 value (ties to even), as a Fraction."""
+    from fractions import Fraction
+    if q == 0:
+        return Fraction(0)
+    a = abs(q)
+    e = math.floor(math.log2(a.numerator) - math.log2(a.denominator))
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    ulp = Fraction(2) ** (max(e, -14) - 10)  # 11 significant bits; subnormals below 2^-14
+    m = a / ulp
+    f = math.floor(m)
+    r = m - f
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and f % 2 == 1):
+        f += 1
+    return (f * ulp) if q > 0 else -(f * ulp)
+
+
+def test_fp16_interpolation_is_correctly_rounded():
+    """The emulated decoder interpolates the latents in binary16 arithmetic: corner weights
+    rounded to FP16, then w00 L00, + w10 L10, + w01 L01, + w11 L11, each multiply and each fused
+    multiply-add rounded once (ties to even). A decoder whose MLP passes 8 of the 16 inputs
+    through exactly (y_j = relu(x_j) - relu(-x_j) with unit weights) exposes the inputs, which
+    are checked against exact rational arithmetic rounded by an independent binary16 rounding,
+    over every texel of a 16 x 16 material (clamped border cells included)."""
+    from fractions import Fraction
+    rng = np.random.default_rng(21)
+    gh = gw = 4
+    R = 4
+    lat = (rng.normal(0, 1, (gh, gw, 16)) * np.exp2(rng.integers(-6, 4, (gh, gw, 16)))).astype(np.float16)
+    idx = np.array([(x | (y << 16)) for y in range(R * gh) for x in range(R * gw)], np.int32)
+    for half in (0, 1):
+        W1 = np.zeros((64, 24))
+        W2 = np.zeros((64, 64))
+        W3 = np.zeros((8, 64))
+        for j in range(8):
+            W1[j, 8 * half + j] = 1.0
+            W1[8 + j, 8 * half + j] = -1.0
+            W2[j, j] = 1.0
+            W2[8 + j, 8 + j] = 1.0
+            W3[j, j] = 1.0
+            W3[j, 8 + j] = -1.0
+        P = np.concatenate([W1.ravel(), np.zeros(64), W2.ravel(), np.zeros(64), W3.ravel(), np.zeros(8)])
+        lat16, w16, b32 = O.nn_pack_inference(lat.astype(np.float32), P)
+        got = O.nn_decode_f32(lat16, R, w16, b32, idx)
+        for b, t in enumerate(idx):
+            ix, iy = int(t) & 0xffff, int(t) >> 16
+            axes = []
+            for i, g in ((ix, gw), (iy, gh)):
+                pos = Fraction(2 * i + 1, 2 * R) - Fraction(1, 2)
+                c0 = math.floor(pos)
+                axes.append((min(max(c0, 0), g - 1), min(max(c0 + 1, 0), g - 1), pos - c0))
+            (x0, x1, fx), (y0, y1, fy) = axes
+            w = [_rn_f16((1 - fx) * (1 - fy)), _rn_f16(fx * (1 - fy)), _rn_f16((1 - fx) * fy), _rn_f16(fx * fy)]
+            cells = [(y0, x0), (y0, x1), (y1, x0), (y1, x1)]
+            for j in range(8):
+                ch = 8 * half + j
+                L = [Fraction(float(lat[cy, cx, ch])) for cy, cx in cells]
+                s = _rn_f16(w[0] * L[0])
+                for k in (1, 2, 3):
+                    s = _rn_f16(w[k] * L[k] + s)
+                assert Fraction(float(got[b, j])) == s, (ix, iy, ch)
