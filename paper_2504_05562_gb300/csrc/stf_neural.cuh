@@ -237,9 +237,9 @@ __device__ __forceinline__ uint32_t nn_chunk(int m, int j, int K) { return (m >>
 //      TMEM); between layers the epilogue warpgroup turns a tile's accumulators into FP16
 //      activations (ReLU) in TMEM, the A operand of the next layer, and arrives on epi[tile]; the
 //      tiles alternate, so one tile's products overlap the other's epilogue;
-//   3. the epilogue warpgroup writes the 8 FP32 outputs of each row over that row's consumed
-//      layer-1 inputs and arrives on out_full[slot]; the client threads read their rows back (and, when
-//      sharing, their warp's other rows).
+//   3. the epilogue warpgroup writes the 8 FP32 outputs of each row into the slot's output planes
+//      and arrives on out_full[slot]; the client threads read their rows back (and, when sharing,
+//      their warp's other rows).
 // Two slots let the clients prepare round r + 1 while round r is decoded. Every wait is bounded:
 // one that gives up counts itself in flags[0], and all later waits of the launch return at once
 // (the outputs are then garbage, and the library reports the timeout).
@@ -262,6 +262,9 @@ struct NnPipeSmem {
     alignas(128) unsigned char io[2][kNnIoBytes];
     float4 rec[2][kNnRows];  // per-row sample records of the clients (see the render kernels)
     float4 geo[2][kNnRows];  // per-row pixel geometry (u, v, cx, cy) of the render clients
+    // decoded channels 0-3 and 4-7 of each row, per slot: a plane per half keeps a warp's 128-bit
+    // reads of its rows conflict-free and their addresses linear in the row
+    float4 out[2][2][kNnRows];
     unsigned long long in_full[2], out_full[2], mma[2], epi[2];  // mma, epi: one barrier per tile
     uint32_t tmem;
     int more[2];             // 1: the round in this slot carries rows, 0: the clients are done
@@ -347,16 +350,11 @@ __device__ __forceinline__ void nn_publish(NnPipeSmem& sm, int slot, int more)
     nn_arrive(smem_u32(&sm.in_full[slot]));
 }
 
-// The decoded outputs of row `row` sit in the row's own layer-1 chunks 0 and 1 (16 bytes each):
-// a row's outputs overwrite only its own inputs, so a client warp writing the next round's rows
-// of this slot never touches another warp's outputs (and 8 lanes read 8 distinct bank groups).
-__device__ __forceinline__ uint32_t nn_out_offset(int row, int half) { return nn_chunk(row, half, kNnK1); }
-
 // The 8 decoded FP32 channels of row `row` (valid after out_full of its round).
 __device__ __forceinline__ void nn_get_outputs(const NnPipeSmem& sm, int slot, int row, float (&t)[8])
 {
-    const float4 a = *reinterpret_cast<const float4*>(sm.io[slot] + nn_out_offset(row, 0));
-    const float4 b = *reinterpret_cast<const float4*>(sm.io[slot] + nn_out_offset(row, 1));
+    const float4 a = sm.out[slot][0][row];
+    const float4 b = sm.out[slot][1][row];
     t[0] = a.x; t[1] = a.y; t[2] = a.z; t[3] = a.w;
     t[4] = b.x; t[5] = b.y; t[6] = b.z; t[7] = b.w;
 }
@@ -544,8 +542,8 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
             tile_wait(mt);
             float o[8];
             tmem_ld8(t_lane + mt * 64, o);
-            *reinterpret_cast<float4*>(sm.io[slot] + nn_out_offset(mt * 128 + m, 0)) = make_float4(o[0], o[1], o[2], o[3]);
-            *reinterpret_cast<float4*>(sm.io[slot] + nn_out_offset(mt * 128 + m, 1)) = make_float4(o[4], o[5], o[6], o[7]);
+            sm.out[slot][0][mt * 128 + m] = make_float4(o[0], o[1], o[2], o[3]);
+            sm.out[slot][1][mt * 128 + m] = make_float4(o[4], o[5], o[6], o[7]);
         }
         tc_fence_before();
         nn_arrive(smem_u32(&sm.out_full[slot]));

@@ -165,8 +165,8 @@ struct NnRenderClient {
                 }
                 const float wt = (src == lane) ? 1.0f : (wx * wy) * m.z;
                 const float2 w2 = make_float2(wt, wt);
-                const float4 t0 = *reinterpret_cast<const float4*>(sm.io[slot] + nn_out_offset(row0 + src, 0));
-                const float4 t1 = *reinterpret_cast<const float4*>(sm.io[slot] + nn_out_offset(row0 + src, 1));
+                const float4 t0 = sm.out[slot][0][row0 + src];
+                const float4 t1 = sm.out[slot][1][row0 + src];
                 a2[0] = __ffma2_rn(w2, make_float2(t0.x, t0.y), a2[0]);
                 a2[1] = __ffma2_rn(w2, make_float2(t0.z, t0.w), a2[1]);
                 a2[2] = __ffma2_rn(w2, make_float2(t1.x, t1.y), a2[2]);
