@@ -255,6 +255,9 @@ constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: layer-1 operand, th
 // 32-bit column, K = 80 -> 40 columns) at 128 and 168.
 constexpr int kNnTmemCols = 256;
 constexpr int kNnHidCol = 128, kNnHidCols = kNnK2 / 2;
+// layer-3 accumulators (N = 16) of tile mt at columns kNnOutCol + 16 mt, apart from the layer-1/2
+// accumulators, so the next round's layer 1 can run while the epilogue reads this round's outputs
+constexpr int kNnOutCol = 224;
 constexpr unsigned kNnWaitLimit = 1u << 20;        // mbarrier polls before a wait gives up
 
 struct NnPipeSmem {
@@ -265,7 +268,8 @@ struct NnPipeSmem {
     // decoded channels 0-3 and 4-7 of each row, per slot: a plane per half keeps a warp's 128-bit
     // reads of its rows conflict-free and their addresses linear in the row
     float4 out[2][2][kNnRows];
-    unsigned long long in_full[2], out_full[2], mma[2], epi[2];  // mma, epi: one barrier per tile
+    // mma: layer-1/2 commits, mma_out: layer-3 commits, epi: activations stored (one per tile)
+    unsigned long long in_full[2], out_full[2], mma[2], mma_out[2], epi[2];
     uint32_t tmem;
     int more[2];             // 1: the round in this slot carries rows, 0: the clients are done
 };
@@ -307,6 +311,8 @@ __device__ __forceinline__ void nn_pipe_setup(NnPipeSmem& sm, const NeuralDev* n
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.out_full[1])), "r"(128) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.mma[0])), "r"(1) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.mma[1])), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.mma_out[0])), "r"(1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.mma_out[1])), "r"(1) : "memory");
     }
     if ((threadIdx.x >> 5) == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -450,25 +456,29 @@ __device__ __forceinline__ void nn_issue_tile_ts(uint32_t d_tmem, uint32_t a_tme
     nn_commit(mbar);
 }
 
-// The MMA warp (lane 0 issues): per round, wait for the clients' rows and for the previous round's
-// outputs to have left TMEM, issue layer 1 of both tiles, then each later layer of a tile as soon
-// as the epilogue warpgroup has stored that tile's activations.
+// The MMA warp (lane 0 issues): per round, wait for the clients' rows, issue layer 1 of both
+// tiles, then each later layer of a tile as soon as the epilogue warpgroup has stored that tile's
+// activations. Layer 1 of round r + 1 overwrites a tile's layer-1/2 accumulators, which the
+// epilogue has read before its arrival that released layer 3 of round r; layer 3 accumulates
+// elsewhere (kNnOutCol), so the next round starts without waiting for round r's outputs.
+// Commits: mma[mt] completes twice per round (layers 1, 2), mma_out[mt] once (layer 3); neither
+// runs more than one phase ahead of the epilogue, which consumes them in issue order.
 __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
 {
     const uint32_t tmem = sm.tmem, b = smem_u32(sm.b);
     const uint32_t bar[2] = {smem_u32(&sm.mma[0]), smem_u32(&sm.mma[1])};
+    const uint32_t bar_out[2] = {smem_u32(&sm.mma_out[0]), smem_u32(&sm.mma_out[1])};
     constexpr uint32_t sbo1 = kNnK1 / 8 * 128, sbo2 = kNnK2 / 8 * 128;
     const uint64_t b1 = nn_sdesc(b, 128, sbo1), b2 = nn_sdesc(b + kNnB1Bytes, 128, sbo2);
     const uint64_t b3 = nn_sdesc(b + kNnB1Bytes + kNnB2Bytes, 128, sbo2);
     const bool leader = (threadIdx.x & 31) == 0;
     NnWaiter w{flags, 0};
-    uint32_t eph[2] = {0u, 0u}, commits = 0;  // products committed per tile
+    uint32_t eph[2] = {0u, 0u}, c12 = 0, c3 = 0;  // commits per tile on mma[] and on mma_out[]
 #pragma unroll 1
     for (uint32_t r = 0;; ++r) {
         const int slot = r & 1;
         w.wait(sm.in_full[slot], (r >> 1) & 1u);
         if (__shfl_sync(0xffffffffu, sm.more[slot], 0) == 0 || __any_sync(0xffffffffu, w.dead)) break;
-        if (r > 0) w.wait(sm.out_full[(r - 1) & 1], ((r - 1) >> 1) & 1u);  // TMEM reads of round r - 1 done
         tc_fence_after();
         const uint32_t io = smem_u32(sm.io[slot]);
         if (leader)
@@ -476,7 +486,8 @@ __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
             for (int mt = 0; mt < 2; ++mt)
                 nn_issue_tile<kNnK1>(tmem + mt * 64, nn_sdesc(io + mt * (kNnRows / 2 / 8) * sbo1, 128, sbo1), b1,
                                      nn_idesc(64), bar[mt]);
-        commits += 3;
+        c12 += 2;
+        c3 += 1;
 #pragma unroll
         for (int layer = 2; layer <= 3; ++layer) {
 #pragma unroll
@@ -487,17 +498,19 @@ __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
                 if (leader) {
                     const uint32_t a = tmem + kNnHidCol + mt * kNnHidCols;
                     if (layer == 2) nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b2, nn_idesc(64), bar[mt]);
-                    else nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b3, nn_idesc(16), bar[mt]);
+                    else nn_issue_tile_ts<kNnK2>(tmem + kNnOutCol + mt * 16, a, b3, nn_idesc(16), bar_out[mt]);
                 }
                 __syncwarp();
             }
         }
     }
-    // after a timeout, products may still be in flight: wait (bounded) for each tile's last commit
-    // before the teardown frees TMEM
-    if (leader && commits > 0 && w.dead)
-        for (int mt = 0; mt < 2; ++mt)
-            for (unsigned it = 0; it < kNnWaitLimit && !nn_try_wait(bar[mt], (commits - 1) & 1u); ++it) {}
+    // after a timeout, products may still be in flight: wait (bounded) for each barrier's last
+    // commit before the teardown frees TMEM
+    if (leader && c12 > 0 && w.dead)
+        for (int mt = 0; mt < 2; ++mt) {
+            for (unsigned it = 0; it < kNnWaitLimit && !nn_try_wait(bar[mt], (c12 - 1) & 1u); ++it) {}
+            for (unsigned it = 0; it < kNnWaitLimit && !nn_try_wait(bar_out[mt], (c3 - 1) & 1u); ++it) {}
+        }
 }
 
 // The epilogue warpgroup: per round and tile, turn layer 1 and 2 accumulators into the next
@@ -515,7 +528,7 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
         tmem_wait_st();
     }
     NnWaiter w{flags, 0};
-    uint32_t ph[2] = {0u, 0u};
+    uint32_t ph[2] = {0u, 0u}, po[2] = {0u, 0u};
     auto tile_wait = [&](int mt) {
         w.wait(sm.mma[mt], ph[mt]);
         ph[mt] ^= 1u;
@@ -539,9 +552,11 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
         }
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
-            tile_wait(mt);
+            w.wait(sm.mma_out[mt], po[mt]);
+            po[mt] ^= 1u;
+            tc_fence_after();
             float o[8];
-            tmem_ld8(t_lane + mt * 64, o);
+            tmem_ld8(t_lane + kNnOutCol + mt * 16, o);
             sm.out[slot][0][mt * 128 + m] = make_float4(o[0], o[1], o[2], o[3]);
             sm.out[slot][1][mt * 128 + m] = make_float4(o[4], o[5], o[6], o[7]);
         }
