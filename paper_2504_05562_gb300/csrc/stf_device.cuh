@@ -168,22 +168,37 @@ template <int F> struct Axis {
     float p;                   // its weight (the 1D PMF value)
 };
 
-// Tap weights only (for the deterministic filter).
+// Tap weights only (for the deterministic filter). Bilinear: c - floor(c) lies in [0, 1] and
+// c - (floor(c) + 1) in [-1, 0], so 1 - |d| is never negative and the clamp of W is dropped
+// (the same floats as w_bilinear).
 template <int F> __device__ __forceinline__ void axis_weights(float c, Axis<F>& A)
 {
     const float i0f = floorf(c);
     A.base = __float2int_rn(i0f) + Taps<F>::K0;
     A.basef = __fadd_rn(i0f, (float)Taps<F>::K0);
 #pragma unroll
-    for (int t = 0; t < Taps<F>::N; ++t) A.w[t] = tap_weight<F>(c, __fadd_rn(A.basef, (float)t), t);
+    for (int t = 0; t < Taps<F>::N; ++t) {
+        const float nf = __fadd_rn(A.basef, (float)t);
+        if constexpr (F == 0) A.w[t] = __fsub_rn(1.0f, fabsf(__fsub_rn(c, nf)));
+        else A.w[t] = tap_weight<F>(c, nf, t);
+    }
 }
 
 // Taps in increasing lattice order; running FP32 CDF; first tap with u < CDF, else the last
-// tap with positive weight.
+// tap with positive weight. Bilinear in closed form: CDF_0 = w0 and CDF_1 = w0 + w1 >= w0, so
+// u >= w0 picks tap 1 whenever w1 > 0 (through the CDF or as the last positive tap) and tap 0
+// otherwise (w0 > 0 then, the weights summing to about 1).
 template <int F> __device__ __forceinline__ void axis_select(float c, float u, Axis<F>& A)
 {
     constexpr int NT = Taps<F>::N;
     axis_weights<F>(c, A);
+    if constexpr (F == 0) {
+        const bool one = !(u < A.w[0]) && A.w[1] > 0.0f;
+        A.n = A.base + (one ? 1 : 0);
+        A.nf = one ? __fadd_rn(A.basef, 1.0f) : A.basef;
+        A.p = one ? A.w[1] : A.w[0];
+        return;
+    }
     float cdf = 0.0f;
     int pick = -1;
 #pragma unroll
