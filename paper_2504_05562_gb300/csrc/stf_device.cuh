@@ -93,10 +93,18 @@ __device__ __forceinline__ float rcp_approx(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// The .ftz forms: the shading inputs are never subnormal (unit vectors, squared lengths of sums
+// of unit vectors, a^2 >= 1.6e-7), so flushing changes no result and saves the subnormal fixups.
 __device__ __forceinline__ float sqrt_approx(float x)
 {
     float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
@@ -385,18 +393,18 @@ __device__ __forceinline__ float4 shade(const DevView& v, float r0, float r1, fl
     // tangent-space normal (X, Y, sqrt(1 - X^2 - Y^2)) has unit length unless |XY| > 1
     const float xy2 = fmaf(nx, nx, ny * ny);
     const float nz = sqrt_approx(fmaxf(1.0f - xy2, 0.0f));
-    const float inl = rsqrtf(fmaxf(xy2, 1.0f));
+    const float inl = rsqrt_approx(fmaxf(xy2, 1.0f));
     const float N0 = nx * inl, N1 = nz * inl, N2 = ny * inl;  // world (x, y, z) = (T, N, B)
     const float P0 = fmaf(v.p2w[0], u, fmaf(v.p2w[1], w, v.p2w[2]));
     const float P2 = fmaf(v.p2w[3], u, fmaf(v.p2w[4], w, v.p2w[5]));
     float V0 = v.cam[0] - P0, V1 = v.cam[1], V2 = v.cam[2] - P2;
-    const float ivl = rsqrtf(fmaf(V0, V0, fmaf(V1, V1, V2 * V2)));
+    const float ivl = rsqrt_approx(fmaf(V0, V0, fmaf(V1, V1, V2 * V2)));
     V0 *= ivl; V1 *= ivl; V2 *= ivl;
     const float L0 = v.light[0], L1 = v.light[1], L2 = v.light[2];
     const float NL = fmaf(N0, L0, fmaf(N1, L1, N2 * L2));
     const float NV = fmaxf(fmaf(N0, V0, fmaf(N1, V1, N2 * V2)), 1e-4f);
     float H0 = L0 + V0, H1 = L1 + V1, H2 = L2 + V2;
-    const float ihl = rsqrtf(fmaf(H0, H0, fmaf(H1, H1, H2 * H2)));
+    const float ihl = rsqrt_approx(fmaf(H0, H0, fmaf(H1, H1, H2 * H2)));
     H0 *= ihl; H1 *= ihl; H2 *= ihl;
     const float NH = fmaxf(fmaf(N0, H0, fmaf(N1, H1, N2 * H2)), 0.0f);
     const float VH = fmaxf(fmaf(V0, H0, fmaf(V1, H1, V2 * H2)), 0.0f);
