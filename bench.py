@@ -389,7 +389,12 @@ def run_ours(a):
         line["reuse_time_over_one_tap"] = extras[a.mode]["ms_median"] / extras["one_tap"]["ms_median"]
         if a.workload == "c3":
             line["estimators"] = estimators_extra(a, stf, torch, tex, view, flush, rank, out, refs["full"])
-        line["e2e"] = e2e(a, stf, torch, mat, view)
+        line["e2e"] = e2e(a, stf, torch, mat, view, direct=True)
+        alt = e2e(a, stf, torch, mat, view, direct=False)
+        line["e2e"]["copy_engine_download"] = {"value": alt["value"], "ms_per_step": alt["ms_per_step"]}
+        if a.workload == "c4":
+            line["e2e"]["note"] = ("measured on the stored FP16 material: a neural material has no per-frame "
+                                   "texel upload")
         if not a.no_neural:
             line["neural"] = neural_extra(a, stf, torch, W, view, flush)
         if not a.no_batch:
@@ -539,29 +544,39 @@ def batch_extra(a, stf, torch, W, tex, flush):
             "gpu_launches_per_batch": 1}
 
 
-def e2e(a, stf, torch, mat, view):
+def e2e(a, stf, torch, mat, view, direct=False, chunks=1):
     """Through the public API with host buffers, per step: the material's texels from pinned host
-    memory into a texture (stf_update_texture), the render, and the frame back into pinned host
-    memory, which the host then reads. Steps are double-buffered over three streams (upload,
-    render, download), so step i + 1's upload and step i - 1's download overlap step i's render;
-    the host waits for each step's frame before its buffers are reused."""
+    memory into a texture (stf_update_texture), the render, and the frame in pinned host memory,
+    which the host then reads. direct: the render kernel stores the frame straight into the
+    pinned host buffer over the CPU-GPU link (the view's out_rgba is the host buffer's address);
+    otherwise it renders into device memory and copy-engine transfers bring the frame back, split
+    into `chunks` row bands on as many streams.
+    Steps are double-buffered over streams (upload, render, and for copies download), so step
+    i + 1's upload overlaps step i's render; the host waits for each step's frame before its
+    buffers are reused."""
     import numpy as np
     plane = mat["planes"][0]
     host = torch.from_numpy(np.ascontiguousarray(plane[2]).view(np.uint8).reshape(-1)).pin_memory()
     texs = [stf.Texture(mat) for _ in range(2)]
-    outs = [torch.empty((a.height, a.width, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
     host_outs = [torch.empty((a.height, a.width, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
-    s_up, s_render, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    outs = host_outs if direct else [torch.empty((a.height, a.width, 4), dtype=torch.float32, device="cuda")
+                                     for _ in range(2)]
+    s_up, s_render = torch.cuda.Stream(), torch.cuda.Stream()
+    s_downs = [torch.cuda.Stream() for _ in range(chunks)]
+    ev_downc = [[torch.cuda.Event() for _ in range(chunks)] for _ in range(2)]
+    rb = [a.height * c // chunks for c in range(chunks + 1)]
     ev_up = [torch.cuda.Event() for _ in range(2)]
     ev_render = [torch.cuda.Event() for _ in range(2)]
     ev_down = [torch.cuda.Event() for _ in range(2)]
+    ev_done = ev_render if direct else ev_down  # the frame is in host memory
+    s_down_join = torch.cuda.Stream()
     steps = max(6, a.steps)
     checksum = 0.0
 
     def step(i):
         k = i % 2
         if i >= 2:
-            ev_down[k].synchronize()           # the host reads step i - 2's frame
+            ev_done[k].synchronize()           # the host reads step i - 2's frame
             nonlocal checksum
             checksum += float(host_outs[k][0, 0, 0])
         s_up.wait_event(ev_render[k])          # the texture's previous render is done
@@ -569,31 +584,37 @@ def e2e(a, stf, torch, mat, view):
         texs[k].update(host)
         ev_up[k].record(s_up)
         s_render.wait_event(ev_up[k])
-        s_render.wait_event(ev_down[k])        # the output's previous download is done
+        if not direct:
+            s_render.wait_event(ev_down[k])    # the output's previous download is done
         stf.set_stream(s_render.cuda_stream)
         stf.render_views([stf.make_view(dict(view, frame=i), texs[k], outs[k])], stf.FILTER_PER_VIEW, MODES[a.mode], 0)
         ev_render[k].record(s_render)
-        s_down.wait_event(ev_render[k])
-        with torch.cuda.stream(s_down):
-            host_outs[k].copy_(outs[k], non_blocking=True)
-        ev_down[k].record(s_down)
+        if not direct:
+            for c in range(chunks):
+                s_downs[c].wait_event(ev_render[k])
+                with torch.cuda.stream(s_downs[c]):
+                    host_outs[k][rb[c]:rb[c + 1]].copy_(outs[k][rb[c]:rb[c + 1]], non_blocking=True)
+                ev_downc[k][c].record(s_downs[c])
+                s_down_join.wait_event(ev_downc[k][c])
+            ev_down[k].record(s_down_join)
 
     for i in range(4):
         step(i)
     for k in range(2):
-        ev_down[k].synchronize()
+        ev_done[k].synchronize()
     t0 = time.perf_counter()
     for i in range(steps):
         step(4 + i)
     for k in range(2):
-        ev_down[k].synchronize()               # the last two frames read back
+        ev_done[k].synchronize()               # the last two frames read back
     dt = (time.perf_counter() - t0) / steps
     stf.set_stream(torch.cuda.current_stream().cuda_stream)
     for t in texs:
         t.close()
     return {"value": a.width * a.height / dt / 1e9, "unit": "Gpix/s", "ms_per_step": dt * 1e3,
             "h2d_bytes_per_step": int(host.numel()), "d2h_bytes_per_step": int(host_outs[0].numel() * 4),
-            "pipelining": "double-buffered upload / render / download streams"}
+            "pipelining": ("double-buffered upload / render streams; the kernel stores the frame into pinned "
+                           "host memory" if direct else "double-buffered upload / render / download streams")}
 
 
 def main():
