@@ -245,9 +245,15 @@ def cpu_baseline(a, mat, view, seconds):
             break
     dt = time.perf_counter() - t0
     px = frames * a.width * a.height
+    # one thread, for scale: a full frame takes a few seconds
+    t1 = time.perf_counter()
+    O.render(mat, dict(view, frame=0), MODES[a.mode], seed=0, nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": px / dt / 1e9, "unit": "Gpix/s", "cores": cores, "kind": "oracle",
             "sample": "%d full frames of the workload (%s), plain C oracle FP32 path, %d threads, %.1f s"
-                      % (frames, a.mode, cores, dt)}
+                      % (frames, a.mode, cores, dt),
+            "single_thread": {"value": a.width * a.height / dt1 / 1e9, "unit": "Gpix/s", "cores": 1,
+                              "sample": "1 full frame, %.1f s" % dt1}}
 
 
 def run_reference(a):
