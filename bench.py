@@ -395,6 +395,7 @@ def run_ours(a):
         line["reuse_time_over_one_tap"] = extras[a.mode]["ms_median"] / extras["one_tap"]["ms_median"]
         if a.workload == "c3":
             line["estimators"] = estimators_extra(a, stf, torch, tex, view, flush, rank, out, refs["full"])
+            line["config2"] = config2_extra(stf, torch, W, flush, rank)
         line["e2e"] = e2e(a, stf, torch, mat, view)
         alt = e2e(a, stf, torch, mat, view, direct=True)  # measured slower on GB300 (10.4 vs 11.3 Gpix/s)
         line["e2e"]["kernel_stores_to_host"] = {"value": alt["value"], "ms_per_step": alt["ms_per_step"]}
@@ -430,6 +431,55 @@ def estimators_extra(a, stf, torch, tex, view, flush, rank, out, full):
             torch.cuda.synchronize()
             res[name + ("_clamped" if clamp else "")] = {"ms_median": statistics.median(tt),
                                                          "psnr_db_vs_full": psnr(torch, img, full)}
+    return res
+
+
+def config2_extra(stf, torch, W, flush, rank):
+    """Config 2: the 1920x1080 perspective ground plane (area magnification 2x-32x) over the
+    1024^2 brick material stored as RGBA8 + RG16F, cubic B-spline, frames 0-15. Median time per
+    mode, PSNR against the full filter, and both rooflines of the reuse mode: the issue bound
+    (algorithmic operations, 6 used channels, projective coordinates) and the HBM bound
+    (algorithmic bytes: the float4 output plus every texel under the union of the pixels' filter
+    supports, counted once)."""
+    import numpy as np
+    mat = W.material_c2()
+    tex = stf.Texture(mat)
+    view = W.config2_view()
+    w, h, size = view["width"], view["height"], mat["width"]
+    out = torch.empty((h, w, 4), dtype=torch.float32, device="cuda")
+    res, refs = {}, {}
+    for name in ("full", "one_tap", "wave2", "wave3", "wave4"):
+        tt = time_mode(stf, torch, tex, view, MODES[name], 16, 3, flush, rank, out)
+        res[name] = {"ms_median": statistics.median(tt)}
+        img = torch.empty_like(out)
+        stf.render_views([stf.make_view(dict(view, frame=0), tex, img)], stf.FILTER_PER_VIEW, MODES[name], 0)
+        refs[name] = img
+    torch.cuda.synchronize()
+    for name in res:
+        res[name]["gpix_s"] = w * h / (res[name]["ms_median"] * 1e-3) / 1e9
+        res[name]["psnr_db_vs_full"] = psnr(torch, refs[name], refs["full"]) if name != "full" else None
+    # texels under the union of the B-spline supports (taps floor(c) - 1 .. floor(c) + 2, clamped)
+    H = np.asarray(view["H"], np.float64).reshape(3, 3)
+    ys, xs = np.mgrid[0:h, 0:w]
+    q = H @ np.stack([xs.ravel() + 0.5, ys.ravel() + 0.5, np.ones(w * h)])
+    cx, cy = q[0] / q[2] * size - 0.5, q[1] / q[2] * size - 0.5
+    used = np.zeros((size, size), bool)
+    for dy in range(-1, 3):
+        for dx in range(-1, 3):
+            used[np.clip(np.floor(cy) + dy, 0, size - 1).astype(np.int64),
+                 np.clip(np.floor(cx) + dx, 0, size - 1).astype(np.int64)] = True
+    alg_bytes = w * h * 16 + int(used.sum()) * 8
+    ms = res["wave3"]["ms_median"]
+    ops = alg_ops_per_pixel("bspline", "wave3", C=6, affine=False) * w * h
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    res["roofline_wave3"] = {
+        "alu": {"achieved_tops": ops / (ms * 1e-3) / 1e12, "peak_tops": alu_peak_ops() / 1e12,
+                "frac": ops / (ms * 1e-3) / alu_peak_ops()},
+        "hbm": {"achieved_gbs": alg_bytes / (ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                "frac": alg_bytes / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes_per_launch": alg_bytes,
+                "unique_texels": int(used.sum())}}
+    tex.close()
     return res
 
 
