@@ -193,36 +193,29 @@ template <int F> __device__ __forceinline__ void axis_weights(float c, Axis<F>& 
 }
 
 // Taps in increasing lattice order; running FP32 CDF; first tap with u < CDF, else the last
-// tap with positive weight. Bilinear in closed form: CDF_0 = w0 and CDF_1 = w0 + w1 >= w0, so
-// u >= w0 picks tap 1 whenever w1 > 0 (through the CDF or as the last positive tap) and tap 0
-// otherwise (w0 > 0 then, the weights summing to about 1).
+// tap with positive weight; both filters in closed form. Bilinear: CDF_0 = w0 and CDF_1 = w0 + w1
+// >= w0, so u >= w0 picks tap 1 whenever w1 > 0 (through the CDF or as the last positive tap)
+// and tap 0 otherwise (w0 > 0 then, the weights summing to about 1). Cubic B-spline: the running
+// CDF never decreases, so the first tap with u < CDF_t is the number k of CDF_0 .. CDF_2 at or
+// below u whenever u < CDF_3; otherwise (rounding left u above the total) the last positive tap
+// is 3, or 2 when w3 = 0 (the middle taps always weigh at least 1/6).
 template <int F> __device__ __forceinline__ void axis_select(float c, float u, Axis<F>& A)
 {
-    constexpr int NT = Taps<F>::N;
     axis_weights<F>(c, A);
     if constexpr (F == 0) {
         const bool one = !(u < A.w[0]) && A.w[1] > 0.0f;
         A.n = A.base + (one ? 1 : 0);
         A.nf = one ? __fadd_rn(A.basef, 1.0f) : A.basef;
         A.p = one ? A.w[1] : A.w[0];
-        return;
+    } else {
+        const float c0 = A.w[0], c1 = __fadd_rn(c0, A.w[1]), c2 = __fadd_rn(c1, A.w[2]);
+        const float c3 = __fadd_rn(c2, A.w[3]);
+        const int k = (u < c0 ? 0 : 1) + (u < c1 ? 0 : 1) + (u < c2 ? 0 : 1);
+        const int pick = k - ((!(u < c3) && !(A.w[3] > 0.0f)) ? 1 : 0);
+        A.n = A.base + pick;
+        A.nf = __fadd_rn(A.basef, __int2float_rn(pick));
+        A.p = pick == 0 ? A.w[0] : (pick == 1 ? A.w[1] : (pick == 2 ? A.w[2] : A.w[3]));
     }
-    float cdf = 0.0f;
-    int pick = -1;
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        cdf = __fadd_rn(cdf, A.w[t]);
-        if (pick < 0 && u < cdf) pick = t;
-    }
-#pragma unroll
-    for (int t = NT - 1; t >= 0; --t)
-        if (pick < 0 && A.w[t] > 0.0f) pick = t;
-    float p = A.w[0];
-#pragma unroll
-    for (int t = 1; t < NT; ++t) p = (pick == t) ? A.w[t] : p;
-    A.n = A.base + pick;
-    A.nf = __fadd_rn(A.basef, __int2float_rn(pick));
-    A.p = p;
 }
 
 // The pixel's two selection uniforms as exact 24-bit dyadic floats: the counter hash pcg4d of
