@@ -537,7 +537,7 @@ def neural_extra(a, stf, torch, W, view, flush):
         stf.render_views([stf.make_view(dict(view, frame=0), ntex, img)], stf.FILTER_PER_VIEW, m, 0)
         imgs[name] = img
         res[name] = {"ms_median": statistics.median(tt), "gpix_s": a.width * a.height / (statistics.median(tt) * 1e-3) / 1e9}
-    # the uncompressed material's full filter is the judge of the neural frames
+    # PSNR of the neural frames is taken against the uncompressed material's full filter
     ref = torch.empty_like(out)
     stf.render_views([stf.make_view(dict(view, frame=0), target, ref)], stf.FILTER_PER_VIEW, MODES["full"], 0)
     torch.cuda.synchronize()
@@ -578,10 +578,10 @@ def batch_extra(a, stf, torch, W, tex, flush):
     t0 = time.perf_counter()
     stf.autotune(cvs, stf.FILTER_PER_VIEW, mode, 0)
     tune_s = time.perf_counter() - t0
-    configs = {}
+    tuned = {}
     for c in cvs:
         k = "%dx%d/s%d" % stf.view_config(c, stf.FILTER_PER_VIEW, mode)
-        configs[k] = configs.get(k, 0) + 1
+        tuned[k] = tuned.get(k, 0) + 1
     b0 = stf.get_stat(stf.STAT_GRAPH_BUILDS)
     tb = time_fn(torch, lambda: stf.render_views(cvs, stf.FILTER_PER_VIEW, mode, 0), 5, 3, flush)
     builds = stf.get_stat(stf.STAT_GRAPH_BUILDS) - b0
@@ -596,7 +596,7 @@ def batch_extra(a, stf, torch, W, tex, flush):
                         "magnification log-uniform 1-64x, bilinear/B-spline per view, FP16 2048^2 material, %s" % a.mode,
             "pixels": px, "ms_median": mb, "gpix_s": px / (mb * 1e-3) / 1e9, "ms_per_view_mean": mb / 64,
             "one_launch_per_view_ms": me, "one_launch_per_view_gpix_s": px / (me * 1e-3) / 1e9,
-            "autotune_s": tune_s, "tuned_configs": configs, "graph_builds_during_timing": builds,
+            "autotune_s": tune_s, "tuned_configs": tuned, "graph_builds_during_timing": builds,
             "gpu_launches_per_batch": 1}
 
 

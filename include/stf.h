@@ -304,7 +304,7 @@ const char* stf_last_error(void);
 /* ------------------------------------------------------------------------------------------
  * Neural texel decoder (the costly per-texel decode that stochastic filtering amortises,
  * Sections 1 and 5.7: neural texture compression). Not a model from the paper, whose
- * compressed-material format is not given; this build's small stand-in:
+ * compressed-material format is not given; the library's small stand-in:
  *   latents: a latent_w x latent_h grid of 16 channels, R = tex_w / latent_w texels per cell
  *            (a power of two <= 16, the same on both axes);
  *   inputs:  the grid bilinearly interpolated at (i + 0.5) / R - 0.5 per axis (clamp-to-edge),
