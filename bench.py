@@ -665,9 +665,18 @@ def e2e(a, stf, torch, mat, view, direct=False, chunks=1):
         ev_done[k].synchronize()               # the last two frames read back
     dt = (time.perf_counter() - t0) / steps
     stf.set_stream(torch.cuda.current_stream().cuda_stream)
+    # the bound: the same frame's bare pinned device-to-host copy, timed alone
+    src = outs[0] if not direct else torch.empty((a.height, a.width, 4), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    tc = time.perf_counter()
+    for _ in range(steps):
+        host_outs[0].copy_(src, non_blocking=True)
+    torch.cuda.synchronize()
+    copy_ms = (time.perf_counter() - tc) / steps * 1e3
     for t in texs:
         t.close()
     return {"value": a.width * a.height / dt / 1e9, "unit": "Gpix/s", "ms_per_step": dt * 1e3,
+            "bare_download_ms": copy_ms, "frac_of_bare_download": copy_ms / (dt * 1e3),
             "h2d_bytes_per_step": int(host.numel()), "d2h_bytes_per_step": int(host_outs[0].numel() * 4),
             "pipelining": ("double-buffered upload / render streams; the kernel stores the frame into pinned "
                            "host memory" if direct else "double-buffered upload / render / download streams")}
