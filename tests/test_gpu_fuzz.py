@@ -65,3 +65,41 @@ def random_case(case):
 def test_random_configuration_matches_oracle(case):
     mat, view, mode, seed = random_case(case)
     run_both(mat, view, mode, seed)
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_neural_configuration_matches_oracle(case):
+    """Randomised views over an exactly decodable neural material (dyadic latents and sparse
+    dyadic weights, so the tensor-core decode equals the oracle's emulation bit for bit): texel
+    choice bit-exact and channels within the stored kinds' bar, with a random number of
+    persistent pipeline blocks (so blocks run from one to many decode rounds)."""
+    from test_gpu_neural import _exact_decoder, _mods
+    stf, neural = _mods()
+    dec, L, P = _exact_decoder(neural)
+    tex = dec.texture()
+    lat16, w16, b32 = O.nn_pack_inference(L, P)
+    mat = O.neural_material(128, 128, lat16, 4, w16, b32)
+    rng = np.random.default_rng(9000 + case)
+    filt = int(rng.integers(0, 2))
+    mag = math.exp(rng.uniform(math.log(0.2), math.log(12.0)))
+    w, h = int(rng.integers(1, 160)), int(rng.integers(1, 96))
+    origin = (float(rng.uniform(-20, 120)), float(rng.uniform(-20, 120)))
+    tile = [(8, 4), (4, 8), (16, 2)][int(rng.integers(0, 3))]
+    view = W.screen_aligned_view(w, h, 128, 128, mag, filt, origin=origin, tile=tile,
+                                 frame=int(rng.integers(0, 65536)))
+    mode = MODES[int(rng.integers(0, len(MODES)))]
+    if filt == 0 and mode not in (O.ONE_TAP, O.FULL) and rng.uniform() < 0.3:
+        mode |= O.FLAG_EXACT
+    seed = int(rng.integers(0, 2 ** 62))
+    stf.set_option(stf.OPT_PIPELINE_BLOCKS, int(rng.integers(1, 7)))
+    try:
+        out, idx, ch = stf.render(tex, view, mode, seed=seed, debug=True)
+        torch.cuda.synchronize()
+        stf.sync()
+    finally:
+        stf.set_option(stf.OPT_PIPELINE_BLOCKS, 0)
+    r_out, r_idx, r_ch = O.render(mat, view, mode, seed=seed, want_channels=True)
+    if (mode & 15) != O.FULL:
+        assert np.array_equal(idx.cpu().numpy().view(np.uint32), r_idx)
+    g, r = ch.cpu().numpy().astype(np.float64), r_ch.astype(np.float64)
+    assert np.all(np.abs(g - r) <= 1e-5 * np.maximum(np.abs(r), 1.0)), float(np.abs(g - r).max())
