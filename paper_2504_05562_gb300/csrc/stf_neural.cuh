@@ -249,10 +249,10 @@ constexpr int kNnClients = kNnClientWarps * 32;    // 256 texels per round
 constexpr int kNnMmaWarp = 8;
 constexpr int kNnRows = 256;                       // operand rows per round (two M = 128 tiles)
 constexpr int kNnPipeThreads = 416;
-constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: layer-1 operand, then each row's 8 FP32 outputs
-// TMEM columns of a block: FP32 accumulators of the two tiles at 0 and 64 (64 columns each), and
-// the tiles' FP16 hidden activations (the A operand of layers 2 and 3, two K elements per
-// 32-bit column, K = 80 -> 40 columns) at 128 and 168.
+constexpr int kNnIoBytes = kNnRows * kNnK1 * 2;    // 16384: the layer-1 operand of a round
+// TMEM columns of a block: layer-1/2 FP32 accumulators of the two tiles at 0 and 64 (64 columns
+// each), the tiles' FP16 hidden activations (the A operand of layers 2 and 3, two K elements per
+// 32-bit column, K = 80 -> 40 columns) at 128 and 168, layer-3 accumulators at 224 and 240.
 constexpr int kNnTmemCols = 256;
 constexpr int kNnHidCol = 128, kNnHidCols = kNnK2 / 2;
 // layer-3 accumulators (N = 16) of tile mt at columns kNnOutCol + 16 mt, apart from the layer-1/2
