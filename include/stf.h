@@ -197,9 +197,16 @@ stf_status stf_render_views(const stf_view* views, int n, int filter, int reuse_
  * captured once into a CUDA graph and replayed while the batch keeps its shape (same views per
  * kind, same item count). */
 enum { STF_OPT_BATCH_GRAPHS = 1,   /* 1 (default): replay CUDA graphs */
-       STF_OPT_PIPELINE_BLOCKS = 2 /* > 0: at most this many persistent blocks for a neural-material
-                                    * view (each then runs more decode rounds); 0 (default): fill the
-                                    * SMs */ };
+       STF_OPT_PIPELINE_BLOCKS = 2, /* > 0: at most this many persistent blocks for a neural-material
+                                     * view (each then runs more decode rounds); 0 (default): fill the
+                                     * SMs */
+       STF_OPT_TEST_DECODE_STALL = 3 /* testing aid for failure detection: 1 makes the next
+                                      * stf_decoder_decode pipeline (the render kernels ignore the
+                                      * switch) withhold its first layer-1 products, so its
+                                      * bounded waits run out (2^20 polls) and every wait of the
+                                      * launch then returns at once; outputs of that launch are
+                                      * garbage and stf_sync reports STF_ERR_TIMEOUT, which also
+                                      * clears the switch. No device fault is involved. */ };
 enum { STF_STAT_GRAPH_BUILDS = 1, STF_STAT_GRAPH_REPLAYS = 2 };
 stf_status stf_set_option(int option, long long value);
 stf_status stf_get_stat(int stat, long long* value);

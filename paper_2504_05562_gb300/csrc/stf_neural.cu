@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kNnPipeThreads, 2) k_nn_decode_list(const Neur
     NnPipeSmem& sm = *reinterpret_cast<NnPipeSmem*>(dyn);
     nn_pipe_setup(sm, nd);
     if (threadIdx.x >= kNnClients) {
-        nn_decode_role(sm, flags);
+        nn_decode_role<true>(sm, flags);
     } else {
         const int row = threadIdx.x;
         NnWaiter w{flags, 0};

@@ -463,6 +463,7 @@ __device__ __forceinline__ void nn_issue_tile_ts(uint32_t d_tmem, uint32_t a_tme
 // elsewhere (kNnOutCol), so the next round starts without waiting for round r's outputs.
 // Commits: mma[mt] completes twice per round (layers 1, 2), mma_out[mt] once (layer 3); neither
 // runs more than one phase ahead of the epilogue, which consumes them in issue order.
+template <bool TEST>
 __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
 {
     const uint32_t tmem = sm.tmem, b = smem_u32(sm.b);
@@ -474,6 +475,10 @@ __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
     const bool leader = (threadIdx.x & 31) == 0;
     NnWaiter w{flags, 0};
     uint32_t eph[2] = {0u, 0u}, c12 = 0, c3 = 0;  // commits per tile on mma[] and on mma_out[]
+    // failure-detection test switch (flags[2], decode-list kernel only): withhold round 0's
+    // layer-1 products, so the epilogue's bounded wait for them runs out
+    bool stall = false;
+    if constexpr (TEST) stall = *reinterpret_cast<volatile int*>(flags + 2) != 0;
 #pragma unroll 1
     for (uint32_t r = 0;; ++r) {
         const int slot = r & 1;
@@ -481,12 +486,13 @@ __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
         if (__shfl_sync(0xffffffffu, sm.more[slot], 0) == 0 || __any_sync(0xffffffffu, w.dead)) break;
         tc_fence_after();
         const uint32_t io = smem_u32(sm.io[slot]);
-        if (leader)
+        const bool withhold = stall && r == 0;
+        if (leader && !withhold)
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
                 nn_issue_tile<kNnK1>(tmem + mt * 64, nn_sdesc(io + mt * (kNnRows / 2 / 8) * sbo1, 128, sbo1), b1,
                                      nn_idesc(64), bar[mt]);
-        c12 += 2;
+        c12 += withhold ? 1 : 2;
         c3 += 1;
 #pragma unroll
         for (int layer = 2; layer <= 3; ++layer) {
@@ -515,6 +521,7 @@ __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
 
 // The epilogue warpgroup: per round and tile, turn layer 1 and 2 accumulators into the next
 // layer's FP16 activations (in TMEM), then write the layer-3 outputs to shared memory.
+template <bool TEST>
 __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
 {
     // row within a tile = TMEM lane: a warp reaches the 32 lanes of quarter (warp id mod 4)
@@ -529,6 +536,10 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
     }
     NnWaiter w{flags, 0};
     uint32_t ph[2] = {0u, 0u}, po[2] = {0u, 0u};
+    // under the failure-detection test switch (flags[2], decode-list kernel only) the warp stops
+    // touching TMEM once a wait has timed out (products may still be running)
+    bool guard = false;
+    if constexpr (TEST) guard = *reinterpret_cast<volatile int*>(flags + 2) != 0;
     auto tile_wait = [&](int mt) {
         w.wait(sm.mma[mt], ph[mt]);
         ph[mt] ^= 1u;
@@ -545,7 +556,10 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
                 tile_wait(mt);
-                nn_hidden_epilogue(t_lane + mt * 64, t_lane + kNnHidCol + mt * kNnHidCols);
+                // after a timeout (test switch) no TMEM access, but the arrivals go on so the other
+                // roles drain
+                if (!(TEST && guard && __any_sync(0xffffffffu, w.dead)))
+                    nn_hidden_epilogue(t_lane + mt * 64, t_lane + kNnHidCol + mt * kNnHidCols);
                 tc_fence_before();
                 nn_arrive(smem_u32(&sm.epi[mt]));
             }
@@ -556,7 +570,15 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
             po[mt] ^= 1u;
             tc_fence_after();
             float o[8];
-            tmem_ld8(t_lane + kNnOutCol + mt * 16, o);
+            if constexpr (TEST) {
+                if (guard && __any_sync(0xffffffffu, w.dead))
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) o[c] = 0.0f;
+                else
+                    tmem_ld8(t_lane + kNnOutCol + mt * 16, o);
+            } else {
+                tmem_ld8(t_lane + kNnOutCol + mt * 16, o);
+            }
             sm.out[slot][0][mt * 128 + m] = make_float4(o[0], o[1], o[2], o[3]);
             sm.out[slot][1][mt * 128 + m] = make_float4(o[4], o[5], o[6], o[7]);
         }
@@ -566,10 +588,12 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
 }
 
 // The decode side of a pipeline block (threads kNnClients .. kNnPipeThreads - 1).
+// TEST: honour the failure-detection test switch (the decode-list kernel).
+template <bool TEST = false>
 __device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
 {
-    if ((threadIdx.x >> 5) == kNnMmaWarp) nn_mma_role(sm, flags);
-    else nn_epilogue_role(sm, flags);
+    if ((threadIdx.x >> 5) == kNnMmaWarp) nn_mma_role<TEST>(sm, flags);
+    else nn_epilogue_role<TEST>(sm, flags);
 }
 
 }  // namespace stf

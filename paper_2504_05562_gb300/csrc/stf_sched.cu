@@ -402,6 +402,15 @@ extern "C" stf_status stf_set_option(int option, long long value)
         if (value < 0 || value > (1 << 20)) return stf_fail(STF_ERR_INVALID_ARG, "pipeline blocks %lld", value);
         g_pipeline_blocks = (int)value;
         return STF_OK;
+    case STF_OPT_TEST_DECODE_STALL: {
+        // flags[2] is read by the MMA warp of each decode pipeline; stf_sync clears all flags
+        int* flags = nullptr;
+        stf_status st = stf_device_state(&flags, nullptr);
+        if (st != STF_OK) return st;
+        const int v = value != 0;
+        cudaError_t e = cudaMemcpy(flags + 2, &v, sizeof v, cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? STF_OK : stf_cuda_fail(e, "test stall switch");
+    }
     }
     return stf_fail(STF_ERR_INVALID_ARG, "unknown option %d", option);
 }

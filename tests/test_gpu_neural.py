@@ -223,3 +223,24 @@ def test_render_neural_material_tight(filt, mode):
         assert np.array_equal(idx.cpu().numpy().view(np.uint32), r_idx)
     g, r = ch.cpu().numpy().astype(np.float64), r_ch.astype(np.float64)
     assert np.all(np.abs(g - r) <= 1e-5 * np.maximum(np.abs(r), 1.0)), float(np.abs(g - r).max())
+
+
+def test_decode_stall_times_out_and_recovers():
+    """Failure detection without a device fault: the test switch makes the next decode pipeline
+    withhold its first layer-1 products, so the epilogue's bounded wait runs out; every role then
+    drains (no TMEM access after the timeout), stf_sync reports STF_ERR_TIMEOUT and clears the
+    switch, and the context stays usable: the next decode equals the oracle bit for bit."""
+    stf, neural = _mods()
+    dec, L, P = _exact_decoder(neural)
+    idx = _all_texels(128, 128)
+    t = torch.from_numpy(idx).cuda()
+    lat16, w16, b32 = O.nn_pack_inference(L, P)
+    ref = O.nn_decode_f32(lat16, 4, w16, b32, idx)
+    stf.set_option(stf.OPT_TEST_DECODE_STALL, 1)
+    dec.decode(t)
+    torch.cuda.synchronize()
+    assert stf.load().stf_sync() == stf.ERR_TIMEOUT
+    assert "gave up" in stf.last_error()
+    out = dec.decode(t).cpu().numpy()
+    stf.sync()
+    assert np.array_equal(out, ref)
