@@ -104,3 +104,19 @@ def test_corrupted_checkpoints_rejected_before_any_gpu_work(tmp_path):
     assert rc != stf.ERR_INVALID_ARG, stf.last_error()
     if rc == stf.OK:
         L.stf_decoder_destroy(h)
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's enum values equal the header's (the binding only marshals)."""
+    import re
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "stf.h")).read()
+    pairs = {
+        "STF_MODE_SPARSE9": stf.MODE_SPARSE9, "STF_MODE_FLAG_EXACT": stf.MODE_FLAG_EXACT,
+        "STF_MODE_FLAG_BLUE_NOISE": stf.MODE_FLAG_BLUE_NOISE, "STF_MODE_EST_SHIFT": stf.MODE_EST_SHIFT,
+        "STF_MODE_FLAG_CLAMP": stf.MODE_FLAG_CLAMP, "STF_OPT_BATCH_GRAPHS": stf.OPT_BATCH_GRAPHS,
+        "STF_OPT_PIPELINE_BLOCKS": stf.OPT_PIPELINE_BLOCKS, "STF_OPT_TEST_DECODE_STALL": stf.OPT_TEST_DECODE_STALL,
+    }
+    for name, value in pairs.items():
+        m = re.search(r"\b%s\s*(?:=\s*)?\(?\s*(\d+)" % name, text)
+        assert m, name
+        assert int(m.group(1)) == value, (name, m.group(1), value)
