@@ -40,7 +40,7 @@ static int device_sms()
 template <int KIND, int F, int MODE, int TW, int TH, bool EX, bool ALT, bool BLUE>
 static cudaError_t launch_one(const DevView& v, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((v.tiles_x + kWarpsPerBlock - 1) / kWarpsPerBlock), (unsigned)v.tiles_y);
+    const dim3 grid((unsigned)((v.tiles_x + kViewWarps - 1) / kViewWarps), (unsigned)v.tiles_y);
     if (grid.x == 0 || grid.y == 0) return cudaSuccess;
     if constexpr (KIND == K_NEURAL) {  // persistent decode-pipeline blocks over the 8-tile groups
         static int cached = 0;
@@ -54,7 +54,7 @@ static cudaError_t launch_one(const DevView& v, cudaStream_t s)
         const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
         k_render_neural<F, MODE, TW, TH, EX, BLUE><<<blocks, kNnPipeThreads, dyn, s>>>(v);
     } else {
-        k_render_view<KIND, F, MODE, TW, TH, EX, ALT, BLUE><<<grid, 32 * kWarpsPerBlock, 0, s>>>(v);
+        k_render_view<KIND, F, MODE, TW, TH, EX, ALT, BLUE><<<grid, 32 * kViewWarps, 0, s>>>(v);
     }
     return cudaGetLastError();
 }
