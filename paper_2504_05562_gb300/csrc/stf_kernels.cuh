@@ -331,9 +331,9 @@ __device__ __forceinline__ void render_tile(const DevView& v, int tx, int ty, in
 // decoded channels); the 48-byte stride keeps 128-bit reads of neighbouring lanes conflict-free.
 constexpr int kRecPerLane = 3;
 
-// Blocks resident per SM the kernel is compiled for (caps registers per thread at 65536 /
-// (256 n)): five 8-warp blocks (<= 51 registers) keep the issue-bound texture kinds at 40 warps
-// per SM.
+// Blocks resident per SM the multi-view kernel (8-warp blocks) is compiled for (caps registers
+// per thread at 65536 / (256 n)): five blocks (<= 51 registers) keep the issue-bound texture
+// kinds at 40 warps per SM.
 constexpr int kMinBlocks = 5;
 
 // The single-view kernel runs 4-warp blocks, ten resident per SM (<= 51 registers): the same 40
