@@ -237,10 +237,13 @@ def test_decode_stall_times_out_and_recovers():
     lat16, w16, b32 = O.nn_pack_inference(L, P)
     ref = O.nn_decode_f32(lat16, 4, w16, b32, idx)
     stf.set_option(stf.OPT_TEST_DECODE_STALL, 1)
-    dec.decode(t)
-    torch.cuda.synchronize()
-    assert stf.load().stf_sync() == stf.ERR_TIMEOUT
-    assert "gave up" in stf.last_error()
+    try:
+        dec.decode(t)
+        torch.cuda.synchronize()
+        assert stf.load().stf_sync() == stf.ERR_TIMEOUT
+        assert "gave up" in stf.last_error()
+    finally:
+        stf.set_option(stf.OPT_TEST_DECODE_STALL, 0)  # never leave the switch on for later tests
     out = dec.decode(t).cpu().numpy()
     stf.sync()
     assert np.array_equal(out, ref)
