@@ -395,7 +395,7 @@ def run_ours(a):
         line["reuse_time_over_one_tap"] = extras[a.mode]["ms_median"] / extras["one_tap"]["ms_median"]
         if a.workload == "c3":
             line["estimators"] = estimators_extra(a, stf, torch, tex, view, flush, rank, out, refs["full"])
-            line["config2"] = config2_extra(stf, torch, W, flush, rank)
+            line["ground_plane_1080p"] = ground_plane_extra(stf, torch, W, flush, rank)
         line["e2e"] = e2e(a, stf, torch, mat, view)
         alt = e2e(a, stf, torch, mat, view, direct=True)  # measured slower on GB300 (10.4 vs 11.3 Gpix/s)
         line["e2e"]["kernel_stores_to_host"] = {"value": alt["value"], "ms_per_step": alt["ms_per_step"]}
@@ -434,8 +434,8 @@ def estimators_extra(a, stf, torch, tex, view, flush, rank, out, full):
     return res
 
 
-def config2_extra(stf, torch, W, flush, rank):
-    """Config 2: the 1920x1080 perspective ground plane (area magnification 2x-32x) over the
+def ground_plane_extra(stf, torch, W, flush, rank):
+    """The 1920x1080 perspective ground plane (area magnification 2x-32x) over the
     1024^2 brick material stored as RGBA8 + RG16F, cubic B-spline, frames 0-15. Median time per
     mode, PSNR against the full filter, and both rooflines of the reuse mode: the issue bound
     (algorithmic operations, 6 used channels, projective coordinates) and the HBM bound
