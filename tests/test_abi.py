@@ -120,3 +120,33 @@ def test_binding_constants_match_the_header():
         m = re.search(r"\b%s\s*(?:=\s*)?\(?\s*(\d+)" % name, text)
         assert m, name
         assert int(m.group(1)) == value, (name, m.group(1), value)
+
+
+def test_autotune_table_round_trip_and_rejections(tmp_path):
+    """The autotune table's text format (host logic, no GPU): a valid table loads and saves back
+    with the same entries; files without the header or with a tile shape or schedule the kernels
+    do not have are rejected and leave the table unchanged."""
+    L = stf.load()
+    assert L.stf_autotune_clear() == stf.OK
+    good = tmp_path / "good.txt"
+    good.write_text("# stf autotune v1 gpu=test\n"
+                    "k3f0m4r2m8 8 4 2 0.012500\n"
+                    "k3f1m4r1m32 4 8 8 0.250000\n"
+                    "k6f1m4r0m2 16 2 1 0.001000\n")
+    assert L.stf_autotune_load(str(good).encode()) == stf.OK
+    out = tmp_path / "saved.txt"
+    assert L.stf_autotune_save(str(out).encode()) == stf.OK
+    lines = out.read_text().splitlines()
+    assert lines[0].startswith("# stf autotune v1")
+    entries = {ln.split()[0]: ln.split()[1:4] for ln in lines[1:]}
+    assert entries == {"k3f0m4r2m8": ["8", "4", "2"], "k3f1m4r1m32": ["4", "8", "8"], "k6f1m4r0m2": ["16", "2", "1"]}
+    for bad in ("k3f0m4r2m8 8 4 2 0.1\n",                                # no header
+                "# stf autotune v1\nk3f0m4r2m8 5 5 2 0.1\n",             # no such tile shape
+                "# stf autotune v1\nk3f0m4r2m8 8 4 0 0.1\n"):            # schedule out of range
+        p = tmp_path / "bad.txt"
+        p.write_text(bad)
+        assert L.stf_autotune_load(str(p).encode()) == stf.ERR_INVALID_ARG
+    assert L.stf_autotune_load(str(tmp_path / "missing.txt").encode()) == stf.ERR_INVALID_ARG
+    assert L.stf_autotune_save(str(out).encode()) == stf.OK
+    assert len(out.read_text().splitlines()) == 4  # unchanged by the rejected loads
+    assert L.stf_autotune_clear() == stf.OK
