@@ -238,8 +238,11 @@ def cpu_baseline(a, mat, view, seconds):
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     frames = 0
+    per_frame = []
     while True:
+        tf = time.perf_counter()
         O.render(mat, dict(view, frame=frames), MODES[a.mode], seed=0, nthreads=cores)
+        per_frame.append(time.perf_counter() - tf)
         frames += 1
         if time.perf_counter() - t0 >= seconds:
             break
@@ -252,6 +255,8 @@ def cpu_baseline(a, mat, view, seconds):
     return {"value": px / dt / 1e9, "unit": "Gpix/s", "cores": cores, "kind": "oracle",
             "sample": "%d full frames of the workload (%s), plain C oracle FP32 path, %d threads, %.1f s"
                       % (frames, a.mode, cores, dt),
+            "ms_per_frame": {"median": statistics.median(per_frame) * 1e3, "min": min(per_frame) * 1e3,
+                             "max": max(per_frame) * 1e3},
             "single_thread": {"value": a.width * a.height / dt1 / 1e9, "unit": "Gpix/s", "cores": 1,
                               "sample": "1 full frame, %.1f s" % dt1}}
 
