@@ -7,7 +7,8 @@
  * texture value sum_i f_r(u - u_i, v - v_i) T_i at the pixel's texture coordinate, then shade.
  * The library estimates it the paper's way: each pixel draws ONE texel with probability equal
  * to its filter weight (one-tap STF, Eq. mc-estimator and Section S1), the pixels of a 32-lane
- * warp tile share their texels with warp shuffles (Section 4.3, Section 4.5), and each pixel
+ * warp tile share their texels through per-warp shared-memory records, the CUDA counterpart of
+ * the paper's wave intrinsics (Section 4.3, Section 4.5), and each pixel
  * combines the shared texels with the bounded weighted importance sampling estimator
  * w_i = f_c(x_i) / f_i(x_i), result = sum_i w_i T_i / sum_j w_j (Eqs. bart-weighted-estimator,
  * estimator-for-stf and estimator-convex, Section 4.2).
@@ -177,8 +178,11 @@ typedef struct {
  * STF_ERR_OUT_OF_MEMORY, STF_ERR_CUDA. *out is set only on success. Synchronous. */
 stf_status stf_create_texture(const stf_texture_desc* desc, stf_texture** out);
 
-/* Renders n views (host array `views`, n >= 1) with one estimator for all of them.
- * `filter` is STF_FILTER_BILINEAR / STF_FILTER_BSPLINE3 for every view, or STF_FILTER_PER_VIEW.
+/* Renders n views (host array `views`, n >= 1) with one estimator for all of them: for every
+ * pixel, the filtered texture value of Eq. texture-continuous-sum (Section 2.1) at the pixel's
+ * texture coordinate, estimated by one-tap STF (Section 2.2, Section S1) and, in the sharing
+ * modes, by the weighted combination of the warp tile's samples (Section 4.2, the loop of
+ * Section 4.5), then shaded. `filter` is STF_FILTER_BILINEAR / STF_FILTER_BSPLINE3 for every view, or STF_FILTER_PER_VIEW.
  * `reuse_mode` is an stf_reuse_mode, optionally | STF_MODE_FLAG_EXACT or an estimator
  * (STF_MODE_EST_SHIFT, STF_MODE_FLAG_CLAMP). `seed` keys the
  * counter-based random stream (pcg4d of
@@ -200,13 +204,19 @@ enum { STF_OPT_BATCH_GRAPHS = 1,   /* 1 (default): replay CUDA graphs */
        STF_OPT_PIPELINE_BLOCKS = 2, /* > 0: at most this many persistent blocks for a neural-material
                                      * view (each then runs more decode rounds); 0 (default): fill the
                                      * SMs */
-       STF_OPT_TEST_DECODE_STALL = 3 /* testing aid for failure detection: 1 makes the next
+       STF_OPT_TEST_DECODE_STALL = 3, /* testing aid for failure detection: 1 makes the next
                                       * stf_decoder_decode pipeline (the render kernels ignore the
                                       * switch) withhold its first layer-1 products, so its
                                       * bounded waits run out (2^20 polls) and every wait of the
                                       * launch then returns at once; outputs of that launch are
                                       * garbage and stf_sync reports STF_ERR_TIMEOUT, which also
-                                      * clears the switch. No device fault is involved. */ };
+                                      * clears the switch. No device fault is involved. */
+       STF_OPT_PAIRED_PIXELS = 4     /* 1 (default): single-view renders of the stored kinds with the
+                                      * bilinear filter (no exact filtering, estimator or blue noise)
+                                      * run two vertically adjacent pixels per thread wherever the
+                                      * pair shares one sharing footprint (same estimates, fewer
+                                      * shared-memory reads and packed arithmetic); 0: one pixel per
+                                      * thread everywhere */ };
 enum { STF_STAT_GRAPH_BUILDS = 1, STF_STAT_GRAPH_REPLAYS = 2 };
 stf_status stf_set_option(int option, long long value);
 stf_status stf_get_stat(int stat, long long* value);
@@ -241,10 +251,12 @@ stf_status stf_autotune_clear(void);
  * enqueued); work items are coarsened to fit STF_NOALLOC_MAX_ITEMS, which changes no pixel;
  * neural-texture views of one call must share one decoder (else STF_ERR_INVALID_ARG).
  * The first call on a device looks up the array's device address and uploads a 1 KB table with
- * a blocking copy, and, unless another entry point ran on the device before, sets up the
- * library's per-device state (error flags, allocated once): make it before any stream capture. All calls share the array (the counters
- * are cleared on each call): calls that overlap on the GPU race. Asynchronous on the library
- * stream otherwise. */
+ * a blocking copy: make it before any stream capture. The per-device error flags the kernels
+ * report through are set up by stf_create_texture; on a device where no texture was created the
+ * call returns STF_ERR_UNSUPPORTED instead of allocating them. All calls share the array (the
+ * counters are cleared on each call): calls that overlap on the GPU race. The host-side staging
+ * is static as well; a lock serialises calls made from several host threads. Asynchronous on the
+ * library stream otherwise. */
 #define STF_NOALLOC_MAX_VIEWS 224
 #define STF_NOALLOC_MAX_ITEMS 262144
 stf_status stf_render_views_noalloc(const stf_view* views, int n, int filter, int reuse_mode,

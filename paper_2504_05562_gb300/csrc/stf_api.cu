@@ -211,6 +211,21 @@ stf_status stf_device_state(int** flags, const float** lut)
     return STF_OK;
 }
 
+// The current device's error flags if its per-device state exists, without setting it up (so
+// without allocating); STF_ERR_UNSUPPORTED otherwise. stf_create_texture sets the state up.
+stf_status stf_device_state_ready(int** flags)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return stf_cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return stf_fail(STF_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    if (!g_dev[dev].ready)
+        return stf_fail(STF_ERR_UNSUPPORTED, "no texture was created on device %d (stf_create_texture sets up the "
+                                             "per-device state)", dev);
+    if (flags) *flags = g_dev[dev].flags;
+    return STF_OK;
+}
+
 extern "C" stf_status stf_sync(void)
 {
     cudaError_t e = cudaStreamSynchronize(g_stream);
@@ -326,7 +341,14 @@ extern "C" stf_status stf_create_texture(const stf_texture_desc* d, stf_texture*
     if (!d || !out) return stf_fail(STF_ERR_INVALID_ARG, "stf_create_texture: null argument");
     if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384)
         return stf_fail(STF_ERR_INVALID_ARG, "texture size %dx%d outside 1..16384", d->width, d->height);
-    if (d->num_planes == 0 && d->decoder) return stf_create_neural_texture(d, out);
+    // the per-device state (error flags, UNORM8 table) is set up with every texture, before its
+    // first allocation, so that rendering (the allocation-free entry point included) never
+    // allocates it later
+    if (d->num_planes == 0 && d->decoder) {
+        stf_status ds = stf_device_state(nullptr, nullptr);
+        if (ds != STF_OK) return ds;
+        return stf_create_neural_texture(d, out);
+    }
     if (d->num_planes < 1 || d->num_planes > 4) return stf_fail(STF_ERR_INVALID_ARG, "num_planes %d outside 1..4", d->num_planes);
     int C = 0;
     for (int p = 0; p < d->num_planes; ++p) {
@@ -360,6 +382,8 @@ extern "C" stf_status stf_create_texture(const stf_texture_desc* d, stf_texture*
         kind = K_U8x4_F16x2;
     }
 
+    stf_status ds = stf_device_state(nullptr, nullptr);
+    if (ds != STF_OK) return ds;
     stf_texture* t = new (std::nothrow) stf_texture();
     if (!t) return stf_fail(STF_ERR_OUT_OF_MEMORY, "host allocation");
     t->width = W; t->height = H; t->channels = C; t->decoder = nullptr;

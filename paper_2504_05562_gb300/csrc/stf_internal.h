@@ -23,6 +23,7 @@ stf_status stf_fail(stf_status s, const char* fmt, ...);
 stf_status stf_cuda_fail(cudaError_t e, const char* what);
 cudaStream_t stf_stream();
 stf_status stf_device_state(int** flags, const float** lut);
+stf_status stf_device_state_ready(int** flags);  // no set-up, no allocation
 stf_status stf_validate_view(const stf_view& v, int i, int filter, int mode);
 void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long long seed, const float* lut,
                       stf::DevView& d);
@@ -45,6 +46,8 @@ bool stf_blue_state(const uint16_t** ranks, int* shift);
 
 // STF_OPT_PIPELINE_BLOCKS (0: fill the SMs).
 extern int g_pipeline_blocks;
+// STF_OPT_PAIRED_PIXELS (1, default: two pixels per thread where the paired path exists).
+extern int g_paired_pixels;
 
 // resident blocks per SM, counted from the kernel's resources (stf_api.cu)
 cudaError_t stf_resident_blocks(const void* kernel, int threads, int dyn_bytes, int* n);

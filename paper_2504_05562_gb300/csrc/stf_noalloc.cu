@@ -14,11 +14,16 @@
 // set-up and a blocking copy of the UNORM8 table, so make that first call before any stream
 // capture). All calls share the array and it keeps the last call's contents: the counters are
 // cleared on every call, and calls that overlap on the GPU (different streams, or the same
-// stream from different threads) race on it.
+// stream from different threads) race on it. The library's per-device error flags, which the
+// kernels report bounded-wait timeouts through, are set up by stf_create_texture; a call on a
+// device where no texture was created is refused rather than allocating them. The host-side
+// staging is static too: a lock (no allocation) serialises calls from several host threads over
+// its fill, upload and launches, so one call's item list is never paired with another's views.
 #include <cuda_runtime.h>
 
 #include <cstddef>
 #include <cstring>
+#include <mutex>
 
 #include "stf.h"
 #include "stf_internal.h"
@@ -59,6 +64,7 @@ constexpr int kMaxDevices = 64;
 NoallocScratch* g_dev_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
 NoallocScratch g_stage;                  // host-side lists (static: no heap use)
 int g_order[STF_NOALLOC_MAX_VIEWS];
+std::mutex g_stage_lock;                 // guards g_stage, g_order and g_dev_ptr
 
 #define STF_KIND_SWITCH_NA(CALL)                                   \
     switch (kind) {                                                \
@@ -85,12 +91,15 @@ cudaError_t set_views_na(int kind, const DevView* views, int n_views, int mode, 
 }
 
 // Once per device, with that device current: the scratch's device address and its UNORM8 table.
-stf_status setup(NoallocScratch** out)
+// Also returns the device's error flags, which must exist already (nothing is allocated here).
+stf_status setup(NoallocScratch** out, int** flags)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return stf_cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return stf_fail(STF_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    stf_status st = stf_device_state_ready(flags);
+    if (st != STF_OK) return st;
     if (!g_dev_ptr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -140,8 +149,10 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
             return stf_fail(STF_ERR_INVALID_ARG, "stf_render_views_noalloc: view %d uses a second neural decoder", i);
         decoder = views[i].tex->decoder;
     }
+    std::lock_guard<std::mutex> hold(g_stage_lock);
     NoallocScratch* dev = nullptr;
-    stf_status st = setup(&dev);
+    int* flags = nullptr;
+    stf_status st = setup(&dev, &flags);
     if (st != STF_OK) return st;
     const float* lut = dev->unorm_lut;
 
@@ -185,6 +196,7 @@ extern "C" stf_status stf_render_views_noalloc(const stf_view* views, int n, int
             const int i = g_order[j];
             DevView& d = g_stage.views[j];
             stf_fill_devview(views[i], filter, reuse_mode, seed, lut, d);
+            d.flags = flags;
             d.tile_w = tw[i];
             d.tile_h = th[i];
             d.tiles_x = (d.width + tw[i] - 1) / tw[i];
