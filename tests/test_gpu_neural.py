@@ -79,9 +79,11 @@ def test_gradients_match_oracle():
     idx = np.array([int(x) | (int(y) << 16) for x, y in rng.integers(0, 64, (777, 2))], np.int32)
     loss_g, dP_g, dl_g = dec.gradients(tex, idx)
     loss_o, dP_o, dl_o = O.nn_loss_grad(L.astype(np.float64), 4, P.astype(np.float64), src, idx)
+    # FP32 forward and backward against FP64: measured within 2e-7 of the largest component on
+    # this case and two others; 1e-5 leaves room for the order of the FP32 sums
     assert abs(loss_g - loss_o) <= 1e-5 * loss_o
-    assert np.max(np.abs(dP_g - dP_o)) <= 2e-3 * np.max(np.abs(dP_o))
-    assert np.max(np.abs(dl_g - dl_o)) <= 2e-3 * np.max(np.abs(dl_o))
+    assert np.max(np.abs(dP_g - dP_o)) <= 1e-5 * np.max(np.abs(dP_o))
+    assert np.max(np.abs(dl_g - dl_o)) <= 1e-5 * np.max(np.abs(dl_o))
     # the parameters did not move
     L2, P2 = dec.get_params()
     assert np.array_equal(L2, L) and np.array_equal(P2, P)
