@@ -211,12 +211,16 @@ enum { STF_OPT_BATCH_GRAPHS = 1,   /* 1 (default): replay CUDA graphs */
                                       * launch then returns at once; outputs of that launch are
                                       * garbage and stf_sync reports STF_ERR_TIMEOUT, which also
                                       * clears the switch. No device fault is involved. */
-       STF_OPT_PAIRED_PIXELS = 4     /* 1 (default): single-view renders of the stored kinds with the
+       STF_OPT_PAIRED_PIXELS = 4,    /* 1 (default): single-view renders of the stored kinds with the
                                       * bilinear filter (no exact filtering, estimator or blue noise)
                                       * run two vertically adjacent pixels per thread wherever the
                                       * pair shares one sharing footprint (same estimates, fewer
                                       * shared-memory reads and packed arithmetic); 0: one pixel per
-                                      * thread everywhere */ };
+                                      * thread everywhere */
+       STF_OPT_TMA_STAGE = 5         /* 1: the paired single-view kernels first stage each block's texel
+                                      * footprint in shared memory with the tensor memory accelerator
+                                      * (cp.async.bulk.tensor), then fetch from there; 0 (default):
+                                      * fetch through the read-only global path. Same pixels. */ };
 enum { STF_STAT_GRAPH_BUILDS = 1, STF_STAT_GRAPH_REPLAYS = 2 };
 stf_status stf_set_option(int option, long long value);
 stf_status stf_get_stat(int stat, long long* value);

@@ -1,6 +1,7 @@
 // C interface of the STF library: argument validation, texture creation and relayout, and
 // dispatch of the render kernels. Declarations and the contract are in include/stf.h.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -458,6 +459,42 @@ extern "C" stf_status stf_create_texture(const stf_texture_desc* d, stf_texture*
     return STF_OK;
 }
 
+// Tensor map over a stored texture's records as a [height][width * R / 4] array of 32-bit
+// words, box 16 texels x 4 rows (the TMA-staged render variant's tile). The encode entry point is
+// taken from the driver through the runtime, so the library links no driver library.
+const CUtensorMap* stf_texture_tmap(const stf_texture* t)
+{
+    if (t->tmap_state) return t->tmap_state > 0 ? &t->tmap : nullptr;
+    t->tmap_state = -1;
+    int rec = 0;
+    switch (t->kind) {
+    case K_F32x4: case K_F16x8: case K_BF16x8: rec = 16; break;
+    case K_F32x8: rec = 32; break;
+    case K_F16x4: case K_E4M3x8: case K_U8x4_F16x2: rec = 8; break;
+    default: return nullptr;
+    }
+    if (((size_t)t->width * rec) % 16 != 0) return nullptr;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return nullptr;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)t->width * rec / 4, (cuuint64_t)t->height};
+    const cuuint64_t strides[1] = {(cuuint64_t)t->width * rec};
+    const cuuint32_t box[2] = {(cuuint32_t)(16 * rec / 4), 4};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&t->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, t->texels, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return nullptr;
+    t->tmap_state = 1;
+    return &t->tmap;
+}
+
 extern "C" stf_status stf_destroy(stf_texture* t)
 {
     if (!t) return STF_OK;
@@ -564,6 +601,7 @@ void stf_fill_devview(const stf_view& v, int filter, int mode, unsigned long lon
     stf_device_state(&d.flags, nullptr);
     d.affine = (v.H[6] == 0.0f && v.H[7] == 0.0f && v.H[8] == 1.0f) ? 1 : 0;
     d.estimator = ((mode >> STF_MODE_EST_SHIFT) & 7) | ((mode & STF_MODE_FLAG_CLAMP) ? 8 : 0);
+    d.tmap_host = g_tma_stage ? stf_texture_tmap(t) : nullptr;
     const uint16_t* r = nullptr;
     int sh = 0;
     if ((mode & STF_MODE_FLAG_BLUE_NOISE) && stf_blue_state(&r, &sh)) {

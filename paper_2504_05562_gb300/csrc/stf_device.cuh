@@ -78,6 +78,8 @@ struct DevView {
     uint32_t blue_offset;     // 24-bit offset of the frame: frame * golden-ratio step + seed (mod 2^24)
     int estimator;            // alternative estimator (kernels compiled with ALT): 1 IS, 2 MIS,
                               // 3 pairwise MIS, 4 regression; + 8: clamp to the texels' range
+    const void* tmap_host;    // host address of the texture's tensor map when the TMA-staged render
+                              // variant is selected (read by the host launcher only), else null
 };
 
 // A run of tiles of one view for the persistent multi-view kernel. variant = filter * 3 + tile
@@ -286,71 +288,117 @@ __device__ __forceinline__ float bf2f(uint32_t bits16) { return __uint_as_float(
 
 template <int KIND> struct Mat;
 
+// A texel record as R / 4 32-bit words, read from global memory (read-only path) or from a
+// shared-memory copy (the staged footprint box of the TMA render variant).
+template <int R> struct Raw { uint32_t w[R / 4]; };
+template <int R> __device__ __forceinline__ Raw<R> ld_record(const void* base, size_t i)
+{
+    Raw<R> r;
+    if constexpr (R == 8) {
+        const uint2 a = __ldg(reinterpret_cast<const uint2*>(base) + i);
+        r.w[0] = a.x; r.w[1] = a.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < R / 16; ++k) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4*>(base) + (R / 16) * i + k);
+            r.w[4 * k] = a.x; r.w[4 * k + 1] = a.y; r.w[4 * k + 2] = a.z; r.w[4 * k + 3] = a.w;
+        }
+    }
+    return r;
+}
+template <int R> __device__ __forceinline__ Raw<R> ld_record_shared(uint32_t addr)
+{
+    Raw<R> r;
+    if constexpr (R == 8) {
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.w[0]), "=r"(r.w[1]) : "r"(addr));
+    } else {
+#pragma unroll
+        for (int k = 0; k < R / 16; ++k)
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(r.w[4 * k]), "=r"(r.w[4 * k + 1]), "=r"(r.w[4 * k + 2]), "=r"(r.w[4 * k + 3])
+                         : "r"(addr + 16 * k));
+    }
+    return r;
+}
+
+// Every kind: C channels from an R-byte record; decode(record, texel) and fetch = decode(load).
 template <> struct Mat<K_F32x4> {
-    static constexpr int C = 4;
+    static constexpr int C = 4, R = 16;
+    __device__ static __forceinline__ void decode(const DevView&, const Raw<R>& r, int, int, float (&t)[C])
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) t[i] = __uint_as_float(r.w[i]);
+    }
     __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
     {
-        const float4 r = __ldg(reinterpret_cast<const float4*>(v.texels) + ((size_t)y * v.tex_w + x));
-        t[0] = r.x; t[1] = r.y; t[2] = r.z; t[3] = r.w;
+        decode(v, ld_record<R>(v.texels, (size_t)y * v.tex_w + x), x, y, t);
     }
 };
 
 template <> struct Mat<K_F32x8> {
-    static constexpr int C = 8;
+    static constexpr int C = 8, R = 32;
+    __device__ static __forceinline__ void decode(const DevView&, const Raw<R>& r, int, int, float (&t)[C])
+    {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = __uint_as_float(r.w[i]);
+    }
     __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
     {
-        const float4* p = reinterpret_cast<const float4*>(v.texels) + 2 * ((size_t)y * v.tex_w + x);
-        const float4 a = __ldg(p), b = __ldg(p + 1);
-        t[0] = a.x; t[1] = a.y; t[2] = a.z; t[3] = a.w; t[4] = b.x; t[5] = b.y; t[6] = b.z; t[7] = b.w;
+        decode(v, ld_record<R>(v.texels, (size_t)y * v.tex_w + x), x, y, t);
     }
 };
 
 template <> struct Mat<K_F16x4> {
-    static constexpr int C = 4;
+    static constexpr int C = 4, R = 8;
+    __device__ static __forceinline__ void decode(const DevView&, const Raw<R>& r, int, int, float (&t)[C])
+    {
+        t[0] = h2f(r.w[0] & 0xffffu); t[1] = h2f(r.w[0] >> 16); t[2] = h2f(r.w[1] & 0xffffu); t[3] = h2f(r.w[1] >> 16);
+    }
     __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
     {
-        const uint2 r = __ldg(reinterpret_cast<const uint2*>(v.texels) + ((size_t)y * v.tex_w + x));
-        t[0] = h2f(r.x & 0xffffu); t[1] = h2f(r.x >> 16); t[2] = h2f(r.y & 0xffffu); t[3] = h2f(r.y >> 16);
+        decode(v, ld_record<R>(v.texels, (size_t)y * v.tex_w + x), x, y, t);
     }
 };
 
 template <> struct Mat<K_F16x8> {
-    static constexpr int C = 8;
+    static constexpr int C = 8, R = 16;
+    __device__ static __forceinline__ void decode(const DevView&, const Raw<R>& r, int, int, float (&t)[C])
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { t[2 * i] = h2f(r.w[i] & 0xffffu); t[2 * i + 1] = h2f(r.w[i] >> 16); }
+    }
     __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
     {
-        const uint4 r = __ldg(reinterpret_cast<const uint4*>(v.texels) + ((size_t)y * v.tex_w + x));
-        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) { t[2 * i] = h2f(w[i] & 0xffffu); t[2 * i + 1] = h2f(w[i] >> 16); }
+        decode(v, ld_record<R>(v.texels, (size_t)y * v.tex_w + x), x, y, t);
     }
 };
 
 template <> struct Mat<K_BF16x8> {
-    static constexpr int C = 8;
+    static constexpr int C = 8, R = 16;
+    __device__ static __forceinline__ void decode(const DevView&, const Raw<R>& r, int, int, float (&t)[C])
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { t[2 * i] = bf2f(r.w[i] & 0xffffu); t[2 * i + 1] = __uint_as_float(r.w[i] & 0xffff0000u); }
+    }
     __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
     {
-        const uint4 r = __ldg(reinterpret_cast<const uint4*>(v.texels) + ((size_t)y * v.tex_w + x));
-        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) { t[2 * i] = bf2f(w[i] & 0xffffu); t[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u); }
+        decode(v, ld_record<R>(v.texels, (size_t)y * v.tex_w + x), x, y, t);
     }
 };
 
 template <> struct Mat<K_E4M3x8> {
-    static constexpr int C = 8;
-    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    static constexpr int C = 8, R = 8;
+    __device__ static __forceinline__ void decode(const DevView& v, const Raw<R>& r, int x, int y, float (&t)[C])
     {
-        const uint2 r = __ldg(reinterpret_cast<const uint2*>(v.texels) + ((size_t)y * v.tex_w + x));
         const float4* sp = reinterpret_cast<const float4*>(
             v.scales + ((size_t)(y >> v.scale_shift) * v.scale_tiles_x + (x >> v.scale_shift)) * 8);
         const float4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
         const float s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-        const uint32_t w[2] = {r.x, r.y};
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> (16 * j)), __NV_E4M3);
+                const __half2_raw h2 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(r.w[i] >> (16 * j)), __NV_E4M3);
                 const float lo = __half2float(__half(__half_raw{h2.x}));
                 const float hi = __half2float(__half(__half_raw{h2.y}));
                 t[4 * i + 2 * j] = __fmul_rn(lo, s[4 * i + 2 * j]);
@@ -358,19 +406,26 @@ template <> struct Mat<K_E4M3x8> {
             }
         }
     }
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        decode(v, ld_record<R>(v.texels, (size_t)y * v.tex_w + x), x, y, t);
+    }
 };
 
 template <> struct Mat<K_U8x4_F16x2> {
-    static constexpr int C = 8;  // 6 used; channels 6 and 7 read as 0
-    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    static constexpr int C = 8, R = 8;  // 6 used; channels 6 and 7 read as 0
+    __device__ static __forceinline__ void decode(const DevView& v, const Raw<R>& r, int, int, float (&t)[C])
     {
-        const uint2 r = __ldg(reinterpret_cast<const uint2*>(v.texels) + ((size_t)y * v.tex_w + x));
 #pragma unroll
-        for (int i = 0; i < 4; ++i) t[i] = __ldg(v.unorm_lut + ((r.x >> (8 * i)) & 255u));
-        t[4] = h2f(r.y & 0xffffu);
-        t[5] = h2f(r.y >> 16);
+        for (int i = 0; i < 4; ++i) t[i] = __ldg(v.unorm_lut + ((r.w[0] >> (8 * i)) & 255u));
+        t[4] = h2f(r.w[1] & 0xffffu);
+        t[5] = h2f(r.w[1] >> 16);
         t[6] = 0.0f;
         t[7] = 0.0f;
+    }
+    __device__ static __forceinline__ void fetch(const DevView& v, int x, int y, float (&t)[C])
+    {
+        decode(v, ld_record<R>(v.texels, (size_t)y * v.tex_w + x), x, y, t);
     }
 };
 
@@ -380,43 +435,50 @@ template <> struct Mat<K_U8x4_F16x2> {
 // denominator uses a^2 (N.H)^2 + |N x H|^2 (equal to (N.H)^2 (a^2 - 1) + 1 for unit vectors),
 // which keeps the specular peak well conditioned in FP32. With irradiance pi the specular term
 // pi * D * Vis * F simplifies to a^2 F / (2 t^2 (g_v + g_l)), t = the GGX denominator.
+// Every step is an explicitly rounded operation (a multiply, an add or a fused multiply-add) so
+// that the compiler contracts nothing: the two-pixel packed version (shade2, one f32x2
+// instruction per step) gives the same bits.
 __device__ __forceinline__ float4 shade(const DevView& v, float r0, float r1, float r2, float nx, float ny,
                                         float rough, float ao, float u, float w)
 {
     // tangent-space normal (X, Y, sqrt(1 - X^2 - Y^2)) has unit length unless |XY| > 1
-    const float xy2 = fmaf(nx, nx, ny * ny);
-    const float nz = sqrt_approx(fmaxf(1.0f - xy2, 0.0f));
+    const float xy2 = fmaf(nx, nx, __fmul_rn(ny, ny));
+    const float nz = sqrt_approx(fmaxf(__fadd_rn(1.0f, -xy2), 0.0f));
     const float inl = rsqrt_approx(fmaxf(xy2, 1.0f));
-    const float N0 = nx * inl, N1 = nz * inl, N2 = ny * inl;  // world (x, y, z) = (T, N, B)
+    const float N0 = __fmul_rn(nx, inl), N1 = __fmul_rn(nz, inl), N2 = __fmul_rn(ny, inl);  // world (x, y, z) = (T, N, B)
     const float P0 = fmaf(v.p2w[0], u, fmaf(v.p2w[1], w, v.p2w[2]));
     const float P2 = fmaf(v.p2w[3], u, fmaf(v.p2w[4], w, v.p2w[5]));
-    float V0 = v.cam[0] - P0, V1 = v.cam[1], V2 = v.cam[2] - P2;
-    const float ivl = rsqrt_approx(fmaf(V0, V0, fmaf(V1, V1, V2 * V2)));
-    V0 *= ivl; V1 *= ivl; V2 *= ivl;
+    float V0 = __fadd_rn(v.cam[0], -P0), V2 = __fadd_rn(v.cam[2], -P2);
+    const float ivl = rsqrt_approx(fmaf(V0, V0, fmaf(v.cam[1], v.cam[1], __fmul_rn(V2, V2))));
+    V0 = __fmul_rn(V0, ivl);
+    const float V1 = __fmul_rn(v.cam[1], ivl);
+    V2 = __fmul_rn(V2, ivl);
     const float L0 = v.light[0], L1 = v.light[1], L2 = v.light[2];
-    const float NL = fmaf(N0, L0, fmaf(N1, L1, N2 * L2));
-    const float NV = fmaxf(fmaf(N0, V0, fmaf(N1, V1, N2 * V2)), 1e-4f);
-    float H0 = L0 + V0, H1 = L1 + V1, H2 = L2 + V2;
-    const float ihl = rsqrt_approx(fmaf(H0, H0, fmaf(H1, H1, H2 * H2)));
-    H0 *= ihl; H1 *= ihl; H2 *= ihl;
-    const float NH = fmaxf(fmaf(N0, H0, fmaf(N1, H1, N2 * H2)), 0.0f);
-    const float VH = fmaxf(fmaf(V0, H0, fmaf(V1, H1, V2 * H2)), 0.0f);
-    const float c0 = fmaf(N1, H2, -N2 * H1), c1 = fmaf(N2, H0, -N0 * H2), c2 = fmaf(N0, H1, -N1 * H0);
-    const float s2 = fmaf(c0, c0, fmaf(c1, c1, c2 * c2));
+    const float NL = fmaf(N0, L0, fmaf(N1, L1, __fmul_rn(N2, L2)));
+    const float NV = fmaxf(fmaf(N0, V0, fmaf(N1, V1, __fmul_rn(N2, V2))), 1e-4f);
+    float H0 = __fadd_rn(L0, V0), H1 = __fadd_rn(L1, V1), H2 = __fadd_rn(L2, V2);
+    const float ihl = rsqrt_approx(fmaf(H0, H0, fmaf(H1, H1, __fmul_rn(H2, H2))));
+    H0 = __fmul_rn(H0, ihl); H1 = __fmul_rn(H1, ihl); H2 = __fmul_rn(H2, ihl);
+    const float NH = fmaxf(fmaf(N0, H0, fmaf(N1, H1, __fmul_rn(N2, H2))), 0.0f);
+    const float VH = fmaxf(fmaf(V0, H0, fmaf(V1, H1, __fmul_rn(V2, H2))), 0.0f);
+    const float c0 = fmaf(N1, H2, -__fmul_rn(N2, H1)), c1 = fmaf(N2, H0, -__fmul_rn(N0, H2));
+    const float c2 = fmaf(N0, H1, -__fmul_rn(N1, H0));
+    const float s2 = fmaf(c0, c0, fmaf(c1, c1, __fmul_rn(c2, c2)));
     rough = fmaxf(rough, 0.02f);
-    const float al = rough * rough;
-    const float a2 = al * al;
-    const float t = fmaf(a2 * NH, NH, s2);
-    const float ia2 = 1.0f - a2;
+    const float al = __fmul_rn(rough, rough);
+    const float a2 = __fmul_rn(al, al);
+    const float t = fmaf(__fmul_rn(a2, NH), NH, s2);
+    const float ia2 = __fadd_rn(1.0f, -a2);
     const float NLp = fmaxf(NL, 0.0f);  // keeps g_v + g_l > 0 (and ps finite) when the pixel is unlit
-    const float gv = NLp * sqrt_approx(fmaf(NV * NV, ia2, a2));
-    const float gl = NV * sqrt_approx(fmaf(NLp * NLp, ia2, a2));
-    const float q = 1.0f - VH;
-    const float q2 = q * q;
-    const float F = fmaf(0.96f, q2 * q2 * q, 0.04f);
-    const float ps = __fdividef(0.5f * a2 * F, t * t * (gv + gl));
-    const float k = NL > 0.0f ? ao * NL : 0.0f;
-    const float kp = k * ps;
+    const float gv = __fmul_rn(NLp, sqrt_approx(fmaf(__fmul_rn(NV, NV), ia2, a2)));
+    const float gl = __fmul_rn(NV, sqrt_approx(fmaf(__fmul_rn(NLp, NLp), ia2, a2)));
+    const float q = __fadd_rn(1.0f, -VH);
+    const float q2 = __fmul_rn(q, q);
+    const float F = fmaf(0.96f, __fmul_rn(__fmul_rn(q2, q2), q), 0.04f);
+    const float ps = __fdividef(__fmul_rn(__fmul_rn(0.5f, a2), F), __fmul_rn(__fmul_rn(t, t), __fadd_rn(gv, gl)));
+    const float ka = __fmul_rn(ao, NL);
+    const float k = NL > 0.0f ? ka : 0.0f;
+    const float kp = __fmul_rn(k, ps);
     return make_float4(fmaf(k, r0, kp), fmaf(k, r1, kp), fmaf(k, r2, kp), 1.0f);
 }
 

@@ -1,6 +1,7 @@
 // Host-side internals shared by the library's translation units (not part of the C interface).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -17,7 +18,16 @@ struct stf_texture {
     const stf_decoder* decoder;     // NEURAL kind
     const void* decoder_params;     // device parameter block of the decoder (NEURAL kind)
     bool widened = false;           // texels converted at creation (no plane-byte updates)
+    // tensor map over the texel records for the TMA-staged render variant, made on first use
+    // (tmap_state 1) or found impossible (-1: a row pitch that is not a multiple of 16 bytes)
+    mutable CUtensorMap tmap;
+    mutable int tmap_state = 0;
 };
+
+// The texture's tensor map (made on first use), or null if its layout has none.
+const CUtensorMap* stf_texture_tmap(const stf_texture* t);
+// STF_OPT_TMA_STAGE (0, default: the read-only global path).
+extern int g_tma_stage;
 
 stf_status stf_fail(stf_status s, const char* fmt, ...);
 stf_status stf_cuda_fail(cudaError_t e, const char* what);

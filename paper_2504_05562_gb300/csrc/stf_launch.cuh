@@ -7,6 +7,7 @@
 
 #include "stf_kernels.cuh"
 #include "stf_nn_render.cuh"
+#include "stf_pair.cuh"
 #include "stf_internal.h"
 
 namespace stf {
@@ -54,6 +55,17 @@ static cudaError_t launch_one(const DevView& v, cudaStream_t s)
         const unsigned blocks = (unsigned)(groups < cap ? groups : cap);
         k_render_neural<F, MODE, TW, TH, EX, BLUE><<<blocks, kNnPipeThreads, dyn, s>>>(v);
     } else {
+        if constexpr (pair_path<KIND, F, MODE, TW, TH, EX, ALT, BLUE>()) {
+            if (g_paired_pixels) {
+                const dim3 g2((unsigned)((v.tiles_x + 2 * kPairWarps - 1) / (2 * kPairWarps)), (unsigned)v.tiles_y);
+                if (v.tmap_host)
+                    k_render_pair_tma<KIND, F, MODE, TW, TH><<<g2, 32 * kPairWarps, 0, s>>>(
+                        *reinterpret_cast<const CUtensorMap*>(v.tmap_host), v);
+                else
+                    k_render_pair<KIND, F, MODE, TW, TH><<<g2, 32 * kPairWarps, 0, s>>>(v);
+                return cudaGetLastError();
+            }
+        }
         k_render_view<KIND, F, MODE, TW, TH, EX, ALT, BLUE><<<grid, 32 * kViewWarps, 0, s>>>(v);
     }
     return cudaGetLastError();
@@ -145,6 +157,41 @@ __global__ void __launch_bounds__(256, kMinBlocks)
     }
 }
 
+// The multi-view kernel on the paired path (pair_path variants): each warp renders two tiles of
+// the work item at a time, one per half-warp; a half-warp without a tile of its own renders the
+// item's first tile as a stand-in, storing nothing, so that both halves reach the warp's
+// barriers. Three resident 8-warp blocks per SM leave the paired path its registers.
+constexpr int kPairBatchMinBlocks = 3;
+template <int KIND, int MODE, int F, int TW, int TH>
+__global__ void __launch_bounds__(256, kPairBatchMinBlocks)
+    k_render_batch_pair(const WorkItem* __restrict__ items, int n_items, int* counter)
+{
+    __shared__ float4 recs[kWarpsPerBlock * 2 * 32 * kRecPerLane];
+    __shared__ float wtabs[F == 1 ? kWarpsPerBlock * 2 * 32 * 8 : 1];
+    __shared__ WorkItem sw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4;
+    const int tile = warp * 2 + half;
+    float4* rec = recs + tile * 32 * kRecPerLane;
+    float* wtab = wtabs + (F == 1 ? tile * 32 * 8 : 0);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int it = atomicAdd(counter, 1);
+            sw = it < n_items ? items[it] : WorkItem{-1, 0, 0, 0};
+        }
+        __syncthreads();
+        const WorkItem w = sw;
+        __syncthreads();  // sw is rewritten by the next pull
+        if (w.view < 0) break;
+        const DevView& v = c_batch_views[w.view];
+        for (int k = 2 * warp; k < w.ntiles; k += 2 * kWarpsPerBlock) {  // warp-uniform
+            const bool live = k + half < w.ntiles;
+            const int t = w.tile0 + (live ? k + half : 0);
+            const int ty = t / v.tiles_x;
+            render_pair<KIND, F, MODE, TW, TH>(v, t - ty * v.tiles_x, ty, lane & 15, rec, wtab, live, GlobalFetch<KIND>{v});
+        }
+    }
+}
+
 struct NnConstViews {
     __device__ __forceinline__ const DevView& operator()(int i) const { return c_batch_views[i]; }
 };
@@ -207,6 +254,14 @@ static cudaError_t launch_batch_v(const WorkItem* items, int n_items, int* count
         }
         k_render_neural_batch<MODE, F, TW, TH, EX, BLUE><<<grid, kNnPipeThreads, dyn, s>>>(items, n_items, counter);
     } else {
+        if constexpr (pair_path<KIND, F, MODE, TW, TH, EX, false, BLUE>()) {
+            if (g_paired_pixels) {
+                if (grid == 0)
+                    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_pair<KIND, MODE, F, TW, TH>, 256, 0);
+                k_render_batch_pair<KIND, MODE, F, TW, TH><<<grid, 256, 0, s>>>(items, n_items, counter);
+                return cudaGetLastError();
+            }
+        }
         if (grid == 0)
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<KIND, MODE, F, TW, TH, EX, BLUE>, 256, 0);
         k_render_batch<KIND, MODE, F, TW, TH, EX, BLUE><<<grid, 256, 0, s>>>(items, n_items, counter);

@@ -369,6 +369,8 @@ int g_use_graphs = 1;
 }  // namespace
 
 int g_pipeline_blocks = 0;  // STF_OPT_PIPELINE_BLOCKS
+int g_paired_pixels = 1;    // STF_OPT_PAIRED_PIXELS
+int g_tma_stage = 0;        // STF_OPT_TMA_STAGE
 
 // The same resolution as `resolve`, with the class key built in a stack buffer (no heap use).
 void stf_resolve_view_config_nohalloc(const stf_view& v, int filter, int mode, int* tw, int* th, int* sched)
@@ -398,6 +400,8 @@ extern "C" stf_status stf_set_option(int option, long long value)
 {
     switch (option) {
     case STF_OPT_BATCH_GRAPHS: g_use_graphs = value != 0; return STF_OK;
+    case STF_OPT_PAIRED_PIXELS: g_paired_pixels = value != 0; return STF_OK;
+    case STF_OPT_TMA_STAGE: g_tma_stage = value != 0; return STF_OK;
     case STF_OPT_PIPELINE_BLOCKS:
         if (value < 0 || value > (1 << 20)) return stf_fail(STF_ERR_INVALID_ARG, "pipeline blocks %lld", value);
         g_pipeline_blocks = (int)value;

@@ -61,7 +61,7 @@ EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_str
            "stf_render_views_noalloc", "stf_sparse_footprints", "stf_set_sparse_footprints",
            "stf_blue_noise_masks", "stf_set_blue_noise", "stf_update_texture")
 NOALLOC_MAX_VIEWS, NOALLOC_MAX_ITEMS = 224, 262144
-OPT_BATCH_GRAPHS, OPT_PIPELINE_BLOCKS, OPT_TEST_DECODE_STALL = 1, 2, 3
+OPT_BATCH_GRAPHS, OPT_PIPELINE_BLOCKS, OPT_TEST_DECODE_STALL, OPT_PAIRED_PIXELS, OPT_TMA_STAGE = 1, 2, 3, 4, 5
 STAT_GRAPH_BUILDS, STAT_GRAPH_REPLAYS = 1, 2
 
 
