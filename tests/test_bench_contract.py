@@ -46,8 +46,9 @@ def test_operation_model_grows_with_the_footprint():
     assert one < counts[0] < counts[1] < counts[2]
     assert bench.alg_ops_per_pixel("bilinear", "wave3") == 342
     assert bench.alg_ops_per_pixel("bspline", "wave3") > 342
-    # the issue peak: 152 SMs x 4 sub-partitions x 32 lanes at 2070 MHz
-    assert abs(bench.alu_peak_ops() - 152 * 4 * 32 * 2070e6) < 1.0
+    # the issue peak: SMs x 4 sub-partitions x 32 lanes at the sampled clock
+    assert abs(bench.alu_peak_ops(2070.0, 152) - 152 * 4 * 32 * 2070e6) < 1.0
+    assert abs(bench.alu_peak_ops(1500.0, 148) - 148 * 4 * 32 * 1500e6) < 1.0
 
 
 def test_traffic_entries_are_keyed_by_current_sources():
