@@ -12,11 +12,15 @@
 //      often each lane appears in the chosen sets; keep the best;
 //   3. coordinate descent: for each lane in turn, switch to whichever of its candidates lowers the
 //      score; sweep until no switch helps.
-// Host code; the tables go to the device with stf_set_sparse_footprints. Random numbers come from
-// splitmix64 (Steele, Lea and Flood 2014), normal variates from the Box-Muller transform.
+// A last pass orders each lane's set for the device's shared-memory banks (order_for_banks); it
+// changes no set. Host code; the tables go to the device with stf_set_sparse_footprints. Random
+// numbers come from splitmix64 (Steele, Lea and Flood 2014), normal variates from the Box-Muller
+// transform.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "stf.h"
@@ -57,6 +61,108 @@ double score(const std::vector<std::vector<std::vector<int>>>& cand, const std::
     double var = 0.0;
     for (int l = 0; l < kLanes; ++l) var += (use[l] - mean) * (use[l] - mean);
     return std::sqrt(var / kLanes);
+}
+
+// Shared-memory replays of one reading step: each lane reads the 48-byte record of the lane it
+// names, as three 16-byte pieces; a quarter-warp's 8 lanes are served together, and record r's
+// piece k sits in bank group (3 r + k) mod 8, so lanes of a quarter that read different records
+// with the same r mod 8 are served one after another (the same record is broadcast).
+int step_replays(const int (&rec)[kLanes])
+{
+    int replays = 0;
+    for (int q = 0; q < 4; ++q) {
+        int worst = 1;
+        for (int g = 0; g < 8; ++g) {
+            int distinct[8], n = 0;
+            for (int l = 8 * q; l < 8 * q + 8; ++l) {
+                if ((rec[l] & 7) != g) continue;
+                bool seen = false;
+                for (int i = 0; i < n; ++i) seen = seen || distinct[i] == rec[l];
+                if (!seen) distinct[n++] = rec[l];
+            }
+            worst = n > worst ? n : worst;
+        }
+        replays += worst - 1;
+    }
+    return replays;
+}
+
+// Orders every lane's shared lanes (its own lane stays first) so that, step by step, the lanes of
+// each quarter-warp read records in distinct bank groups: per step, a maximum matching of the
+// quarter's lanes to bank groups among their remaining entries (augmenting paths, lanes and
+// entries tried in a random order), the unmatched lanes taking the entry that adds the fewest
+// replays; the best of `tries` randomised schedules per quarter is kept. Only the reading order
+// changes: every lane keeps its set, so the estimate is the same sum taken in another order.
+void order_for_banks(std::vector<std::vector<int>>& rows, SplitMix64& rng, int tries)
+{
+    const int n = (int)rows[0].size();
+    for (int q = 0; q < 4; ++q) {
+        std::vector<std::vector<int>> best;
+        int best_cost = 1 << 30;
+        for (int t = 0; t < tries && best_cost > 0; ++t) {
+            std::vector<std::vector<int>> left(8), out(8);
+            for (int i = 0; i < 8; ++i) {
+                left[i].assign(rows[8 * q + i].begin() + 1, rows[8 * q + i].end());
+                out[i].push_back(rows[8 * q + i][0]);
+                for (int k = (int)left[i].size() - 1; k > 0; --k)  // random order of the entries
+                    std::swap(left[i][k], left[i][(int)(rng.next() % (uint64_t)(k + 1))]);
+            }
+            int cost = 0;
+            for (int s = 1; s < n; ++s) {
+                // lanes -> bank groups (match_g[g] = lane, choice[lane] = entry index)
+                int match_g[8], choice[8];
+                for (int g = 0; g < 8; ++g) match_g[g] = -1;
+                for (int i = 0; i < 8; ++i) choice[i] = -1;
+                int order[8];
+                for (int i = 0; i < 8; ++i) order[i] = i;
+                for (int k = 7; k > 0; --k) std::swap(order[k], order[(int)(rng.next() % (uint64_t)(k + 1))]);
+                for (int oi = 0; oi < 8; ++oi) {
+                    bool visited[8] = {false};
+                    // augmenting path from lane order[oi] (depth-first, explicit recursion)
+                    struct Aug {
+                        std::vector<std::vector<int>>& left; int* match_g; int* choice; bool* visited;
+                        bool run(int lane)
+                        {
+                            for (int e = 0; e < (int)left[lane].size(); ++e) {
+                                const int g = left[lane][e] & 7;
+                                if (visited[g]) continue;
+                                visited[g] = true;
+                                if (match_g[g] < 0 || run(match_g[g])) {
+                                    match_g[g] = lane;
+                                    choice[lane] = e;
+                                    return true;
+                                }
+                            }
+                            return false;
+                        }
+                    } aug{left, match_g, choice, visited};
+                    aug.run(order[oi]);
+                }
+                int rec[kLanes];
+                for (int l = 0; l < kLanes; ++l) rec[l] = l;  // other quarters: conflict-free stand-ins
+                for (int i = 0; i < 8; ++i)
+                    if (choice[i] >= 0) rec[8 * q + i] = left[i][choice[i]];
+                for (int i = 0; i < 8; ++i) {
+                    if (choice[i] >= 0) continue;
+                    int pick = 0, pick_cost = 1 << 30;
+                    for (int e = 0; e < (int)left[i].size(); ++e) {
+                        rec[8 * q + i] = left[i][e];
+                        const int c = step_replays(rec);
+                        if (c < pick_cost) { pick_cost = c; pick = e; }
+                    }
+                    choice[i] = pick;
+                    rec[8 * q + i] = left[i][pick];
+                }
+                cost += step_replays(rec);
+                for (int i = 0; i < 8; ++i) {
+                    out[i].push_back(left[i][choice[i]]);
+                    left[i].erase(left[i].begin() + choice[i]);
+                }
+            }
+            if (cost < best_cost) { best_cost = cost; best = out; }
+        }
+        for (int i = 0; i < 8; ++i) rows[8 * q + i] = best[i];
+    }
 }
 
 }  // namespace
@@ -127,6 +233,7 @@ extern "C" stf_status stf_sparse_footprints(int tile_w, int tile_h, int count, d
                 for (int l = 0; l < kLanes; ++l) best[l] = cand[l][pick[l]];
             }
         }
+        order_for_banks(best, rng, 64);
         for (int l = 0; l < kLanes; ++l)
             for (int i = 0; i < count; ++i) table[((size_t)pat * kLanes + l) * count + i] = (signed char)best[l][i];
         if (scores) scores[pat] = best_score;

@@ -104,3 +104,30 @@ def test_blue_noise_argument_checks():
     mat = W.material_c1()
     with pytest.raises(ValueError):
         O.render(mat, W.screen_aligned_view(8, 4, 64, 64, 2.0, 0), O.ONE_TAP | O.FLAG_BLUE)  # no masks
+
+
+def test_temporal_average_converges_faster_than_white_noise():
+    """The masks' time axis (a golden-ratio rotation of each pixel's uniforms per frame, the
+    reading this build takes of the paper's spatiotemporal masks): averaging one-tap frames over
+    time (as temporal accumulation does) converges faster than with the white-noise hash, whose
+    per-pixel variance only falls as 1/N. Measured on the oracle: 16 frames, white 45.9 dB, blue
+    53.7 dB; from 4 to 16 frames the blue average's MSE falls by more than the 4x of white noise."""
+    mat = W.material_c1()
+    view = W.screen_aligned_view(128, 128, 64, 64, 4.0, 0, origin=(3.3, 7.6))
+    ref = O.render_exact_f64(mat, view)[0][..., :3]
+    masks = stf.blue_noise_masks(64, quad_energy=True, seed=1)
+
+    def mse(n, blue):
+        acc = np.zeros_like(ref)
+        for f in range(n):
+            v = dict(view, frame=f)
+            if blue:
+                acc += O.render(mat, dict(v, blue=masks), O.ONE_TAP | O.FLAG_BLUE, seed=0)[0][..., :3]
+            else:
+                acc += O.render(mat, v, O.ONE_TAP, seed=0)[0][..., :3]
+        return np.mean((acc / n - ref) ** 2)
+
+    white4, white16 = mse(4, False), mse(16, False)
+    blue4, blue16 = mse(4, True), mse(16, True)
+    assert 10 * np.log10(white16 / blue16) > 3.0
+    assert blue4 / blue16 > 1.5 * white4 / white16
