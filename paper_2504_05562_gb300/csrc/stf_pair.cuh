@@ -362,15 +362,17 @@ __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, in
 }
 
 // Warps per block of the paired single-view kernel (each warp renders two tiles) and the blocks
-// it is compiled to keep resident per SM (caps registers at 65536 / (128 n) per thread).
+// it is compiled to keep resident per SM (caps registers at 65536 / (128 n) per thread): eight
+// for one-tap (64 registers, no spills; measured 0.0577 against 0.0598 ms at six on the 4K
+// frame), six for the sharing modes and the full filter (more blocks gained nothing there).
 constexpr int kPairWarps = 4;
-constexpr int kPairMinBlocks = 6;
+template <int MODE> constexpr int pair_min_blocks() { return MODE == 1 ? 8 : 6; }
 
 // One view, paired path: block (bx, by) renders tiles 2 (bx kPairWarps + warp) + half of tile row
 // by. A tile past the row's end (right edge of the grid) is rendered with every store skipped,
 // so that both half-warps reach the warp's barriers.
 template <int KIND, int F, int MODE, int TW, int TH>
-__global__ void __launch_bounds__(32 * kPairWarps, kPairMinBlocks) k_render_pair(const DevView v)
+__global__ void __launch_bounds__(32 * kPairWarps, pair_min_blocks<MODE>()) k_render_pair(const DevView v)
 {
     __shared__ float4 recs[kPairWarps * 2 * 32 * kRecPerLane];
     __shared__ float wtabs[F == 1 ? kPairWarps * 2 * 32 * 8 : 1];
@@ -430,7 +432,7 @@ __device__ __forceinline__ bool tma_wait(uint32_t bar, uint32_t parity)
 }
 
 template <int KIND, int F, int MODE, int TW, int TH>
-__global__ void __launch_bounds__(32 * kPairWarps, kPairMinBlocks)
+__global__ void __launch_bounds__(32 * kPairWarps, pair_min_blocks<MODE>())
     k_render_pair_tma(const __grid_constant__ CUtensorMap tmap, const DevView v)
 {
     constexpr int R = Mat<KIND>::R;
