@@ -125,31 +125,27 @@ cudaError_t launch_view_kind(const DevView& v, int mode, cudaStream_t s)
 // kernel parameters, at no issue cost.
 static __constant__ DevView c_batch_views[kBatchMaxViews];
 
-// Persistent multi-view kernel for one (filter, tile shape) variant: each block pulls work items
+// Persistent multi-view kernel for one (filter, tile shape) variant: each warp pulls work items
 // (a run of tiles of one view) from a device counter until the list is exhausted. Nothing waits
-// on another block, so no wait can stall. One kernel per variant keeps the code of a launch as
-// small as a single-view kernel's.
+// on another warp or block, so no wait can stall. One kernel per variant keeps the code of a
+// launch as small as a single-view kernel's.
 template <int KIND, int MODE, int F, int TW, int TH, bool EX, bool BLUE>
 __global__ void __launch_bounds__(256, kMinBlocks)
     k_render_batch(const WorkItem* __restrict__ items, int n_items, int* counter)
 {
     __shared__ float4 recs[kWarpsPerBlock * 32 * kRecPerLane];
     __shared__ float wtabs[kWarpsPerBlock * 32 * 8];
-    __shared__ WorkItem sw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float4* rec = recs + warp * 32 * kRecPerLane;
     float* wtab = wtabs + warp * 32 * 8;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const int it = atomicAdd(counter, 1);
-            sw = it < n_items ? items[it] : WorkItem{-1, 0, 0, 0};
-        }
-        __syncthreads();
-        const WorkItem w = sw;
-        __syncthreads();  // sw is rewritten by the next pull
-        if (w.view < 0) break;
+    for (;;) {  // every warp pulls its own items
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;  // warp-uniform
+        const WorkItem w = items[it];
         const DevView& v = c_batch_views[w.view];
-        for (int k = warp; k < w.ntiles; k += kWarpsPerBlock) {
+        for (int k = 0; k < w.ntiles; ++k) {
             const int t = w.tile0 + k;
             const int ty = t / v.tiles_x;
             render_tile<KIND, F, MODE, TW, TH, EX, false, BLUE>(v, t - ty * v.tiles_x, ty, lane, rec, wtab);
@@ -157,10 +153,11 @@ __global__ void __launch_bounds__(256, kMinBlocks)
     }
 }
 
-// The multi-view kernel on the paired path (pair_path variants): each warp renders two tiles of
-// the work item at a time, one per half-warp; a half-warp without a tile of its own renders the
-// item's first tile as a stand-in, storing nothing, so that both halves reach the warp's
-// barriers. Three resident 8-warp blocks per SM leave the paired path its registers.
+// The multi-view kernel on the paired path (pair_path variants): every warp pulls work items on
+// its own (no block barrier, so no warp waits for another's tiles) and renders two tiles of its
+// item at a time, one per half-warp; a half-warp without a tile of its own renders the item's
+// first tile as a stand-in, storing nothing, so that both halves reach the warp's barriers. Three
+// resident 8-warp blocks per SM leave the paired path its registers.
 constexpr int kPairBatchMinBlocks = 3;
 template <int KIND, int MODE, int F, int TW, int TH>
 __global__ void __launch_bounds__(256, kPairBatchMinBlocks)
@@ -168,22 +165,18 @@ __global__ void __launch_bounds__(256, kPairBatchMinBlocks)
 {
     __shared__ float4 recs[kWarpsPerBlock * 2 * 32 * kRecPerLane];
     __shared__ float wtabs[F == 1 ? kWarpsPerBlock * 2 * 32 * 8 : 1];
-    __shared__ WorkItem sw;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, half = lane >> 4;
     const int tile = warp * 2 + half;
     float4* rec = recs + tile * 32 * kRecPerLane;
     float* wtab = wtabs + (F == 1 ? tile * 32 * 8 : 0);
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int it = atomicAdd(counter, 1);
-            sw = it < n_items ? items[it] : WorkItem{-1, 0, 0, 0};
-        }
-        __syncthreads();
-        const WorkItem w = sw;
-        __syncthreads();  // sw is rewritten by the next pull
-        if (w.view < 0) break;
+        int it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_items) break;  // warp-uniform
+        const WorkItem w = items[it];
         const DevView& v = c_batch_views[w.view];
-        for (int k = 2 * warp; k < w.ntiles; k += 2 * kWarpsPerBlock) {  // warp-uniform
+        for (int k = 0; k < w.ntiles; k += 2) {  // warp-uniform
             const bool live = k + half < w.ntiles;
             const int t = w.tile0 + (live ? k + half : 0);
             const int ty = t / v.tiles_x;
