@@ -19,9 +19,11 @@
  * Compile with -ffp-contract=off: each float operation below is rounded once, in the order
  * written. Selection decisions (which texel) depend only on this op sequence.
  *
- * Parity unpinned: the exact pcg4d output stream. No published test vectors for it were
- * available, so it is pinned only by its statistics (uniformity, independence, distinct
- * streams) and written from the published definition; the GPU implements the same definition.
+ * pcg4d (the sample source) is pinned without published test vectors: its output, run back
+ * through the inverse of the published steps, gives the input back (a wrong constant, shift,
+ * lane index or dropped step fails this), and its avalanche and the uniforms' statistics
+ * (uniformity, independence, distinct streams) are checked; the GPU implements the same
+ * definition.
  */
 #include "stf_oracle.h"
 
