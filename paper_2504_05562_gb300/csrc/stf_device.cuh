@@ -131,10 +131,12 @@ template <int F> struct Taps;
 template <> struct Taps<0> { static constexpr int N = 2, K0 = 0; };   // bilinear: floor(c) + {0, 1}
 template <> struct Taps<1> { static constexpr int N = 4, K0 = -1; };  // cubic B-spline: floor(c) + {-1..2}
 
-// Bilinear tent per axis, clamp(1 - |d|, 0, 1) (Section S5). 1 - |d| never exceeds 1.
+// Bilinear tent per axis, clamp(1 - |d|, 0, 1) (Section S5). 1 - |d| never exceeds 1, so the
+// clamp is the subtraction's saturation (one instruction; NaN and negative results give +0,
+// as max(., 0) would).
 __device__ __forceinline__ float w_bilinear(float d)
 {
-    return fmaxf(__fsub_rn(1.0f, fabsf(d)), 0.0f);
+    return __saturatef(__fsub_rn(1.0f, fabsf(d)));
 }
 
 // B-spline branches of W with a = |d|: r1 for a < 1, r2 for 1 <= a < 2 (each step rounded once).

@@ -312,8 +312,8 @@ __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, in
                     float2 wx, wy;
                     if constexpr (F == 0) {  // W(c - n) evaluated as the oracle does
                         const float2 dx = add2(cx, f2(-m.x)), dy = add2(cy, f2(-m.y));
-                        wx = make_float2(fmaxf(__fsub_rn(1.0f, fabsf(dx.x)), 0.0f), fmaxf(__fsub_rn(1.0f, fabsf(dx.y)), 0.0f));
-                        wy = make_float2(fmaxf(__fsub_rn(1.0f, fabsf(dy.x)), 0.0f), fmaxf(__fsub_rn(1.0f, fabsf(dy.y)), 0.0f));
+                        wx = make_float2(w_bilinear(dx.x), w_bilinear(dx.y));
+                        wy = make_float2(w_bilinear(dy.x), w_bilinear(dy.y));
                     } else {
                         // the same values read from each pixel's taps: lattice points outside the
                         // taps have zero weight
