@@ -122,7 +122,7 @@ def algorithmic_bytes(a):
 # the sources whose code a kernel's DRAM traffic depends on (its body, helpers and launch)
 TRAFFIC_SOURCES = {
     "k_render_view": ["stf_device.cuh", "stf_kernels.cuh", "stf_launch.cuh"],
-    "k_render_pair": ["stf_device.cuh", "stf_kernels.cuh", "stf_launch.cuh", "stf_pair.cuh", "stf_neural.cuh"],
+    "k_render_pair": ["stf_device.cuh", "stf_kernels.cuh", "stf_launch.cuh", "stf_pair.cuh"],
     "k_render_neural": ["stf_device.cuh", "stf_kernels.cuh", "stf_launch.cuh", "stf_neural.cuh", "stf_nn_render.cuh"],
 }
 

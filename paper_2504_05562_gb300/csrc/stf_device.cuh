@@ -110,6 +110,9 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return r;
 }
 
+// Shared-memory address of a generic pointer to shared memory (for PTX operands).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 // ------------------------------------------------------------------------------ RNG
 
 // pcg4d (Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020): LCG step on the

@@ -127,7 +127,6 @@ __device__ __forceinline__ void nn_inputs(const NeuralDev& nd, int x, int y, uin
 
 // ------------------------------------------------------------------------------ tcgen05 primitives
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor, K-major without swizzle: start address, leading (K) byte
 // offset between core matrices, stride (M/N) byte offset between 8-row groups, version 1.

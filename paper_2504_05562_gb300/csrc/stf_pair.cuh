@@ -18,7 +18,6 @@
 #include <cuda.h>
 
 #include "stf_kernels.cuh"
-#include "stf_neural.cuh"
 
 namespace stf {
 
