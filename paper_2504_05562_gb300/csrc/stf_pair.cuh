@@ -63,12 +63,12 @@ template <int MODE, int TW, int TH> __host__ __device__ constexpr bool pair_rows
     return true;
 }
 
-// The paired path covers the stored kinds with the weighted estimator, without exact filtering
-// or blue noise; everything else renders one pixel per thread.
+// The paired path covers the stored kinds with the weighted estimator, with hash or blue-noise
+// uniforms, without exact filtering; everything else renders one pixel per thread.
 template <int KIND, int F, int MODE, int TW, int TH, bool EX, bool ALT, bool BLUE>
 __host__ __device__ constexpr bool pair_path()
 {
-    return KIND != K_NEURAL && !EX && !ALT && !BLUE && pair_rows_share<MODE, TW, TH>();
+    return KIND != K_NEURAL && !EX && !ALT && pair_rows_share<MODE, TW, TH>();
 }
 
 // pixel_uv / texel_coord for the pixels (x, y) and (x, y + 1), the same rounded steps per element.
@@ -212,7 +212,7 @@ template <int KIND> struct GlobalFetch {
 // and 2 (hl / TW) + 1; rec holds the tile's 32 lane records (3 x 16 bytes each), wtab (B-spline)
 // its lanes' tap weights, fetch reads a texel (clamp-to-edge). All 16 threads of the half-warp
 // (and of the whole warp) execute every shared-memory step.
-template <int KIND, int F, int MODE, int TW, int TH, class FETCH = GlobalFetch<KIND>>
+template <int KIND, int F, int MODE, int TW, int TH, bool BLUE = false, class FETCH = GlobalFetch<KIND>>
 __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, int hl, float4* rec, float* wtab,
                                             bool live, const FETCH& fetch)
 {
@@ -255,8 +255,8 @@ __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, in
     } else {
         // one-tap STF per pixel (Section 2.2, Section S1)
         float uxa, uya, uxb, uyb;
-        pixel_uniforms<false>(v, x, y, uxa, uya);
-        pixel_uniforms<false>(v, x, y + 1, uxb, uyb);
+        pixel_uniforms<BLUE>(v, x, y, uxa, uya);
+        pixel_uniforms<BLUE>(v, x, y + 1, uxb, uyb);
         Axis<F> xa, ya, xb, yb;
         axis_select<F>(cx.x, uxa, xa);
         axis_select<F>(cy.x, uya, ya);
@@ -368,9 +368,9 @@ constexpr int kPairWarps = 4;
 template <int MODE> constexpr int pair_min_blocks() { return MODE == 1 ? 8 : 6; }
 
 // One view, paired path: block (bx, by) renders tiles 2 (bx kPairWarps + warp) + half of tile row
-// by. A tile past the row's end (right edge of the grid) is rendered with every store skipped,
+// by. BLUE: blue-noise selection uniforms. A tile past the row's end (right edge of the grid) is rendered with every store skipped,
 // so that both half-warps reach the warp's barriers.
-template <int KIND, int F, int MODE, int TW, int TH>
+template <int KIND, int F, int MODE, int TW, int TH, bool BLUE = false>
 __global__ void __launch_bounds__(32 * kPairWarps, pair_min_blocks<MODE>()) k_render_pair(const DevView v)
 {
     __shared__ float4 recs[kPairWarps * 2 * 32 * kRecPerLane];
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(32 * kPairWarps, pair_min_blocks<MODE>()) k_re
     const int t0 = (blockIdx.x * kPairWarps + warp) * 2;
     if (t0 >= v.tiles_x) return;  // warp-uniform
     const int half = lane >> 4, tile = warp * 2 + half;
-    render_pair<KIND, F, MODE, TW, TH>(v, t0 + half, blockIdx.y, lane & 15, recs + tile * 32 * kRecPerLane,
+    render_pair<KIND, F, MODE, TW, TH, BLUE>(v, t0 + half, blockIdx.y, lane & 15, recs + tile * 32 * kRecPerLane,
                                        wtabs + (F == 1 ? tile * 32 * 8 : 0), true, GlobalFetch<KIND>{v});
 }
 
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(32 * kPairWarps, pair_min_blocks<MODE>())
     const int t0 = tb + warp * 2;
     if (t0 >= v.tiles_x) return;  // warp-uniform, after the block-wide barrier
     const int half = lane >> 4, tile = warp * 2 + half;
-    render_pair<KIND, F, MODE, TW, TH>(v, t0 + half, blockIdx.y, lane & 15, recs + tile * 32 * kRecPerLane,
+    render_pair<KIND, F, MODE, TW, TH, false>(v, t0 + half, blockIdx.y, lane & 15, recs + tile * 32 * kRecPerLane,
                                        wtabs + (F == 1 ? tile * 32 * 8 : 0), true,
                                        StagedFetch<KIND>{v, smem_u32(box), g.x, g.y, g.z, g.w});
 }
