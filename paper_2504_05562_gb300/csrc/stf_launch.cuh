@@ -58,14 +58,14 @@ static cudaError_t launch_one(const DevView& v, cudaStream_t s)
         if constexpr (pair_path<KIND, F, MODE, TW, TH, EX, ALT, BLUE>()) {
             if (g_paired_pixels) {
                 const dim3 g2((unsigned)((v.tiles_x + 2 * kPairWarps - 1) / (2 * kPairWarps)), (unsigned)v.tiles_y);
-                if constexpr (!BLUE) {
+                if constexpr (!BLUE && !EX) {
                     if (v.tmap_host) {
                         k_render_pair_tma<KIND, F, MODE, TW, TH><<<g2, 32 * kPairWarps, 0, s>>>(
                             *reinterpret_cast<const CUtensorMap*>(v.tmap_host), v);
                         return cudaGetLastError();
                     }
                 }
-                k_render_pair<KIND, F, MODE, TW, TH, BLUE><<<g2, 32 * kPairWarps, 0, s>>>(v);
+                k_render_pair<KIND, F, MODE, TW, TH, BLUE, EX><<<g2, 32 * kPairWarps, 0, s>>>(v);
                 return cudaGetLastError();
             }
         }
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256, kMinBlocks)
 // first tile as a stand-in, storing nothing, so that both halves reach the warp's barriers. Three
 // resident 8-warp blocks per SM leave the paired path its registers.
 constexpr int kPairBatchMinBlocks = 3;
-template <int KIND, int MODE, int F, int TW, int TH, bool BLUE>
+template <int KIND, int MODE, int F, int TW, int TH, bool BLUE, bool EX>
 __global__ void __launch_bounds__(256, kPairBatchMinBlocks)
     k_render_batch_pair(const WorkItem* __restrict__ items, int n_items, int* counter)
 {
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256, kPairBatchMinBlocks)
             const bool live = k + half < w.ntiles;
             const int t = w.tile0 + (live ? k + half : 0);
             const int ty = t / v.tiles_x;
-            render_pair<KIND, F, MODE, TW, TH, BLUE>(v, t - ty * v.tiles_x, ty, lane & 15, rec, wtab, live, GlobalFetch<KIND>{v});
+            render_pair<KIND, F, MODE, TW, TH, BLUE, EX>(v, t - ty * v.tiles_x, ty, lane & 15, rec, wtab, live, GlobalFetch<KIND>{v});
         }
     }
 }
@@ -253,8 +253,8 @@ static cudaError_t launch_batch_v(const WorkItem* items, int n_items, int* count
         if constexpr (pair_path<KIND, F, MODE, TW, TH, EX, false, BLUE>()) {
             if (g_paired_pixels) {
                 if (grid == 0)
-                    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_pair<KIND, MODE, F, TW, TH, BLUE>, 256, 0);
-                k_render_batch_pair<KIND, MODE, F, TW, TH, BLUE><<<grid, 256, 0, s>>>(items, n_items, counter);
+                    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_pair<KIND, MODE, F, TW, TH, BLUE, EX>, 256, 0);
+                k_render_batch_pair<KIND, MODE, F, TW, TH, BLUE, EX><<<grid, 256, 0, s>>>(items, n_items, counter);
                 return cudaGetLastError();
             }
         }

@@ -64,11 +64,12 @@ template <int MODE, int TW, int TH> __host__ __device__ constexpr bool pair_rows
 }
 
 // The paired path covers the stored kinds with the weighted estimator, with hash or blue-noise
-// uniforms, without exact filtering; everything else renders one pixel per thread.
+// uniforms, with or without exact filtering of the bilinear filter; everything else (the
+// alternative estimators, the neural material) renders one pixel per thread.
 template <int KIND, int F, int MODE, int TW, int TH, bool EX, bool ALT, bool BLUE>
 __host__ __device__ constexpr bool pair_path()
 {
-    return KIND != K_NEURAL && !EX && !ALT && pair_rows_share<MODE, TW, TH>();
+    return KIND != K_NEURAL && (!EX || F == 0) && !ALT && pair_rows_share<MODE, TW, TH>();
 }
 
 // pixel_uv / texel_coord for the pixels (x, y) and (x, y + 1), the same rounded steps per element.
@@ -212,7 +213,7 @@ template <int KIND> struct GlobalFetch {
 // and 2 (hl / TW) + 1; rec holds the tile's 32 lane records (3 x 16 bytes each), wtab (B-spline)
 // its lanes' tap weights, fetch reads a texel (clamp-to-edge). All 16 threads of the half-warp
 // (and of the whole warp) execute every shared-memory step.
-template <int KIND, int F, int MODE, int TW, int TH, bool BLUE = false, class FETCH = GlobalFetch<KIND>>
+template <int KIND, int F, int MODE, int TW, int TH, bool BLUE = false, bool EX = false, class FETCH = GlobalFetch<KIND>>
 __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, int hl, float4* rec, float* wtab,
                                             bool live, const FETCH& fetch)
 {
@@ -302,6 +303,7 @@ __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, in
 #pragma unroll
             for (int c = 0; c < C / 2; ++c) { acca[c] = f2(0.0f); accb[c] = f2(0.0f); }
             float2 wsum = f2(0.0f);
+            uint32_t srcsa = 0, srcsb = 0;  // exact filtering: per bilinear tap, 1 + a lane holding its texel
 #pragma unroll
             for (int r = 0; r < FP::KY; ++r) {
 #pragma unroll
@@ -313,6 +315,19 @@ __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, in
                         const float2 dx = add2(cx, f2(-m.x)), dy = add2(cy, f2(-m.y));
                         wx = make_float2(w_bilinear(dx.x), w_bilinear(dx.y));
                         wy = make_float2(w_bilinear(dy.x), w_bilinear(dy.y));
+                        if constexpr (EX) {
+                            const uint32_t pj = __float_as_uint(m.w);
+                            const int kxa = unpack_x(pj) - xa.base, kya = unpack_y(pj) - ya.base;
+                            const int kxb = unpack_x(pj) - xb.base, kyb = unpack_y(pj) - yb.base;
+                            if (((kxa | kya) & ~1) == 0) {
+                                const int sh = 8 * (2 * kya + kxa);
+                                srcsa = (srcsa & ~(0xffu << sh)) | ((uint32_t)(src + 1) << sh);
+                            }
+                            if (((kxb | kyb) & ~1) == 0) {
+                                const int sh = 8 * (2 * kyb + kxb);
+                                srcsb = (srcsb & ~(0xffu << sh)) | ((uint32_t)(src + 1) << sh);
+                            }
+                        }
                     } else {
                         // the same values read from each pixel's taps: lattice points outside the
                         // taps have zero weight
@@ -350,6 +365,19 @@ __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, in
                 ra[2 * c] = qa.x; ra[2 * c + 1] = qa.y;
                 rb[2 * c] = qb.x; rb[2 * c + 1] = qb.y;
             }
+            if constexpr (EX && F == 0) {
+                // exact filtering (Section 4.2): a pixel whose four bilinear taps were all drawn in
+                // its window gets the full filter from those records instead of the estimate
+                auto rec_texel = [&](int j, float (&T)[C]) {
+                    const float4 t0 = rec[kRecPerLane * j + 1];
+                    const float4 t1 = C > 4 ? rec[kRecPerLane * j + 2] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    const float tt[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+                    for (int c = 0; c < C; ++c) T[c] = tt[c];
+                };
+                exact_bilinear<C>(xa, ya, srcsa, ra, rec_texel);
+                exact_bilinear<C>(xb, yb, srcsb, rb, rec_texel);
+            }
             __syncwarp();  // records are rewritten by the warp's next tiles
         }
     }
@@ -368,9 +396,9 @@ constexpr int kPairWarps = 4;
 template <int MODE> constexpr int pair_min_blocks() { return MODE == 1 ? 8 : 6; }
 
 // One view, paired path: block (bx, by) renders tiles 2 (bx kPairWarps + warp) + half of tile row
-// by. BLUE: blue-noise selection uniforms. A tile past the row's end (right edge of the grid) is rendered with every store skipped,
+// by. BLUE: blue-noise selection uniforms; EX: exact filtering (bilinear). A tile past the row's end (right edge of the grid) is rendered with every store skipped,
 // so that both half-warps reach the warp's barriers.
-template <int KIND, int F, int MODE, int TW, int TH, bool BLUE = false>
+template <int KIND, int F, int MODE, int TW, int TH, bool BLUE = false, bool EX = false>
 __global__ void __launch_bounds__(32 * kPairWarps, pair_min_blocks<MODE>()) k_render_pair(const DevView v)
 {
     __shared__ float4 recs[kPairWarps * 2 * 32 * kRecPerLane];
@@ -379,7 +407,7 @@ __global__ void __launch_bounds__(32 * kPairWarps, pair_min_blocks<MODE>()) k_re
     const int t0 = (blockIdx.x * kPairWarps + warp) * 2;
     if (t0 >= v.tiles_x) return;  // warp-uniform
     const int half = lane >> 4, tile = warp * 2 + half;
-    render_pair<KIND, F, MODE, TW, TH, BLUE>(v, t0 + half, blockIdx.y, lane & 15, recs + tile * 32 * kRecPerLane,
+    render_pair<KIND, F, MODE, TW, TH, BLUE, EX>(v, t0 + half, blockIdx.y, lane & 15, recs + tile * 32 * kRecPerLane,
                                        wtabs + (F == 1 ? tile * 32 * 8 : 0), true, GlobalFetch<KIND>{v});
 }
 
@@ -495,7 +523,7 @@ __global__ void __launch_bounds__(32 * kPairWarps, pair_min_blocks<MODE>())
     const int t0 = tb + warp * 2;
     if (t0 >= v.tiles_x) return;  // warp-uniform, after the block-wide barrier
     const int half = lane >> 4, tile = warp * 2 + half;
-    render_pair<KIND, F, MODE, TW, TH, false>(v, t0 + half, blockIdx.y, lane & 15, recs + tile * 32 * kRecPerLane,
+    render_pair<KIND, F, MODE, TW, TH, false, false>(v, t0 + half, blockIdx.y, lane & 15, recs + tile * 32 * kRecPerLane,
                                        wtabs + (F == 1 ? tile * 32 * 8 : 0), true,
                                        StagedFetch<KIND>{v, smem_u32(box), g.x, g.y, g.z, g.w});
 }
