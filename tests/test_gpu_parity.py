@@ -232,6 +232,33 @@ def test_update_texture_equals_new_texture():
         widened.update(np.zeros(64 * 64 * 8, np.uint8))
 
 
+@pytest.mark.parametrize("flag", ["exact", "blue"])
+@pytest.mark.parametrize("mode", [O.QUAD2, O.WAVE3, O.WAVE4])
+def test_paired_exact_and_blue_noise_equal_one_pixel_per_thread(mode, flag):
+    """Exact filtering and blue-noise uniforms on the paired path against one pixel per thread:
+    the same texel choice bit for bit, the same filtered channels within rounding, shaded colours
+    within the shading tolerance, on the 4K FP16 frame and a ragged screen."""
+    stf = _stf()
+    if flag == "blue":
+        stf.set_blue_noise(stf.blue_noise_masks(64, seed=5))
+    m = mode | (stf.MODE_FLAG_EXACT if flag == "exact" else stf.MODE_FLAG_BLUE_NOISE)
+    for mat, view in ((W.material_c3(W.FP16), W.config3_view(0, frame=1)),
+                      (W.material_c1(), W.screen_aligned_view(250, 123, 64, 64, 3.3, 0, origin=(5.2, 7.9), frame=3))):
+        tex = stf.Texture(mat)
+        got = {}
+        for paired in (1, 0):
+            stf.set_option(stf.OPT_PAIRED_PIXELS, paired)
+            try:
+                got[paired] = [t.cpu().numpy() for t in stf.render(tex, view, m, seed=8, debug=True)]
+            finally:
+                stf.set_option(stf.OPT_PAIRED_PIXELS, 1)
+        torch.cuda.synchronize()
+        stf.sync()
+        assert np.array_equal(got[1][1], got[0][1])
+        assert_close(got[1][2], got[0][2], "channels", channel_scale(mat))
+        assert_close(got[1][0], got[0][0], "rgba", 1e-3)
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_paired_path_equals_one_pixel_per_thread(mode):
     """Two pixels per thread (STF_OPT_PAIRED_PIXELS, the default) against one pixel per thread on
