@@ -135,6 +135,14 @@ def _bind_neural(L):
     L.stf_ref_f16_round.restype = C.c_float
     L.stf_ref_f32_to_f16.argtypes = [C.c_float]
     L.stf_ref_f32_to_f16.restype = C.c_uint16
+    L.stf_ref_f64_to_e4m3.argtypes = [C.c_double]
+    L.stf_ref_f64_to_e4m3.restype = C.c_uint8
+    L.stf_ref_e4m3_to_f64.argtypes = [C.c_uint8]
+    L.stf_ref_e4m3_to_f64.restype = C.c_double
+    L.stf_ref_neural_e4m3_scales.argtypes = [dp, ci, ci, dp, dp]
+    L.stf_ref_neural_e4m3_scales.restype = ci
+    L.stf_ref_neural_decode_e4m3.argtypes = [dp, ci, ci, ci, dp, dp, ci, dp, dp]
+    L.stf_ref_neural_decode_e4m3.restype = ci
 
 
 NN_IN, NN_H, NN_OUT, NN_LAT = 24, 64, 8, 16
@@ -213,6 +221,37 @@ def nn_decode_f32(lat16, R, w16, b32, idx):
     idx = np.ascontiguousarray(idx, np.int32)
     out = np.zeros((idx.size, NN_OUT), np.float32)
     lib().stf_ref_neural_decode(_p(lat16), gw, gh, R, _p(w16), w16.size, _p(b32), _p(idx), idx.size, _p(out))
+    return out
+
+
+def e4m3_encode(x):
+    """OCP E4M3 code of x: nearest, ties to the even code, saturating at +-448."""
+    return int(lib().stf_ref_f64_to_e4m3(float(x)))
+
+
+def e4m3_value(code):
+    return float(lib().stf_ref_e4m3_to_f64(int(code)))
+
+
+def nn_e4m3_scales(lat16, P):
+    """Exponents (log2 s1, log2 s2, log2 s3, log2 of the output scale) of the E4M3 variant."""
+    lat16 = np.ascontiguousarray(lat16, np.uint16)
+    gh, gw = lat16.shape[:2]
+    P32 = np.ascontiguousarray(P, np.float32)
+    e = np.zeros(4, np.int32)
+    lib().stf_ref_neural_e4m3_scales(_p(lat16), gw, gh, _p(P32), _p(e))
+    return [int(v) for v in e]
+
+
+def nn_decode_e4m3(lat16, R, P, idx):
+    """Emulation of the E4M3 inference variant (FP16 layer 1, E4M3 hidden layers and weights of
+    layers 2 and 3, FP32 accumulation) from the FP16 latent grid and the FP32 parameters."""
+    lat16 = np.ascontiguousarray(lat16, np.uint16)
+    gh, gw = lat16.shape[:2]
+    P32 = np.ascontiguousarray(P, np.float32)
+    idx = np.ascontiguousarray(idx, np.int32)
+    out = np.zeros((idx.size, NN_OUT), np.float32)
+    lib().stf_ref_neural_decode_e4m3(_p(lat16), gw, gh, R, _p(P32), _p(idx), idx.size, _p(out), None)
     return out
 
 

@@ -83,6 +83,9 @@ typedef struct {
 } ref_material;
 
 /* Neural decoder (stf_oracle_neural.c). */
+int stf_ref_neural_e4m3_scales(const uint16_t* lat16, int GW, int GH, const float* P32, int* e);
+int stf_ref_neural_decode_e4m3(const uint16_t* lat16, int GW, int GH, int R, const float* P32, const int* idx,
+                               int n, float* out, int* e_out);
 int stf_ref_neural_decode(const uint16_t* lat16, int GW, int GH, int R, const uint16_t* w16, int nw,
                           const float* b32, const int* idx, int n, float* out);
 

@@ -20,6 +20,11 @@
  *                  interpolated latents computed in FP16 arithmetic, the 8 position features and
  *                  both hidden layers rounded to FP16, products accumulated in FP32, biases and
  *                  output in FP32.
+ *   E4M3 emulation the FP8 inference variant: layer 1 as above with its weights and bias scaled
+ *                  by a power of two s1; both hidden layers, W2 and W3 rounded to OCP E4M3 after
+ *                  power-of-two scalings (s2, s3) chosen from a first-order bound of the
+ *                  activations so that nothing saturates; each bias of layers 2 and 3 split into
+ *                  three E4M3 parts; products accumulated in FP32; the output scaled back.
  */
 #include <math.h>
 #include <stdint.h>
@@ -314,6 +319,204 @@ int stf_ref_neural_decode_f64(const double* lat, int GW, int GH, int R, const do
     for (int b = 0; b < n; ++b) {
         features_f64(lat, GW, GH, R, idx[b] & 0xffff, idx[b] >> 16, x);
         mlp_f64(P, x, a1, a2, out + (size_t)b * NN_OUT);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------ E4M3 variant */
+
+/* OCP 8-bit E4M3 ("FN"): 1 sign, 4 exponent bits biased by 7, 3 fraction bits, no infinities,
+ * largest finite 448 (code 0x7e), 0x7f / 0xff NaN; exponent field 0 holds the subnormals
+ * m * 2^-9. */
+static double e4m3_value(int code)
+{
+    int s = (code >> 7) & 1, e = (code >> 3) & 15, f = code & 7;
+    double r;
+    if (e == 15 && f == 7) return NAN;
+    if (e == 0) r = ldexp((double)f, -9);
+    else r = ldexp((double)(8 + f), e - 10);
+    return s ? -r : r;
+}
+
+/* Round to nearest E4M3, ties to the even code, saturating to +-448 (the rounding of the GPU's
+ * satfinite conversion); NaN gives 0x7f. Plain search over the 127 finite magnitudes. */
+static uint8_t e4m3_encode(double x)
+{
+    if (isnan(x)) return 0x7f;
+    const int neg = signbit(x) ? 1 : 0;
+    const double a = fabs(x);
+    int best = 0;
+    double berr = INFINITY;
+    for (int c = 0; c <= 0x7e; ++c) {
+        const double err = fabs(e4m3_value(c) - a);
+        if (err < berr || (err == berr && (c & 1) == 0)) { best = c; berr = err; }
+    }
+    return (uint8_t)(best | (neg << 7));
+}
+
+static double e4m3_round(double x) { return e4m3_value(e4m3_encode(x)); }
+
+uint8_t stf_ref_f64_to_e4m3(double x) { return e4m3_encode(x); }
+double stf_ref_e4m3_to_f64(uint8_t c) { return e4m3_value(c); }
+
+/* floor(log2(v)) for v > 0, exactly (frexp: v = f 2^e, f in [0.5, 1)). */
+static int floor_log2(double v)
+{
+    int e;
+    (void)frexp(v, &e);
+    return e - 1;
+}
+
+/* The power-of-two exponents of the E4M3 variant (e[0] = log2 s1, e[1] = log2 s2, e[2] = log2 s3,
+ * e[3] = -(e[0] + e[1] + e[2]), the output scale), from the FP16 latent grid and the FP32
+ * parameters; every sum in FP64, terms in index order. With m = 1.0625 (one E4M3 rounding; it
+ * also covers the FP16 roundings of layer 1):
+ *   xmax_k   max over the grid of |latent k| for k < 16, 1 for the 8 position features;
+ *   B1_j     m (sum_k |W1_jk| xmax_k) + |b1_j|              bounds |h1_j|;
+ *   B2_i     m^2 (sum_j |W2_ij| B1_j) + |b2_i|              bounds |h2_i|;
+ *   s1       2^floor(log2(448 / max_j B1_j)), at most 2^8;
+ *   s2       2^floor(log2(min(448 / (s1 max B2), 448 / max |W2|))), so that s1 s2 h2 and s2 W2
+ *            stay in range (the biases of layer 2 are covered by B2);
+ *   s3       2^floor(log2(min(448 / max |W3|, 448 / (s1 s2 max |b3|)))).
+ * Returns 0. */
+int stf_ref_neural_e4m3_scales(const uint16_t* lat16, int GW, int GH, const float* P32, int* e)
+{
+    const float* W1 = P32;
+    const float* b1 = W1 + NN_H * NN_IN;
+    const float* W2 = b1 + NN_H;
+    const float* b2 = W2 + NN_H * NN_H;
+    const float* W3 = b2 + NN_H;
+    const float* b3 = W3 + NN_OUT * NN_H;
+    const double m = 1.0625;
+    double xmax[NN_IN];
+    for (int k = 0; k < NN_IN; ++k) xmax[k] = k < NN_LAT ? 0.0 : 1.0;
+    for (long long c = 0; c < (long long)GW * GH; ++c)
+        for (int k = 0; k < NN_LAT; ++k) {
+            const double v = fabs((double)h2f(lat16[c * NN_LAT + k]));
+            if (v > xmax[k]) xmax[k] = v;
+        }
+    double B1[NN_H], maxB1 = 0.0, maxB2 = 0.0, maxW2 = 0.0, maxW3 = 0.0, maxb3 = 0.0;
+    for (int j = 0; j < NN_H; ++j) {
+        double t = 0.0;
+        for (int k = 0; k < NN_IN; ++k) t += fabs((double)W1[j * NN_IN + k]) * xmax[k];
+        B1[j] = m * t + fabs((double)b1[j]);
+        if (B1[j] > maxB1) maxB1 = B1[j];
+    }
+    for (int i = 0; i < NN_H; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < NN_H; ++j) {
+            t += fabs((double)W2[i * NN_H + j]) * B1[j];
+            if (fabs((double)W2[i * NN_H + j]) > maxW2) maxW2 = fabs((double)W2[i * NN_H + j]);
+        }
+        const double b2i = m * m * t + fabs((double)b2[i]);
+        if (b2i > maxB2) maxB2 = b2i;
+    }
+    for (int k = 0; k < NN_OUT * NN_H; ++k)
+        if (fabs((double)W3[k]) > maxW3) maxW3 = fabs((double)W3[k]);
+    for (int o = 0; o < NN_OUT; ++o)
+        if (fabs((double)b3[o]) > maxb3) maxb3 = fabs((double)b3[o]);
+    int e1 = maxB1 > 0.0 ? floor_log2(448.0 / maxB1) : 8;
+    if (e1 > 8) e1 = 8;
+    double lim2 = maxW2 > 0.0 ? 448.0 / maxW2 : INFINITY;
+    if (maxB2 > 0.0 && 448.0 / (ldexp(1.0, e1) * maxB2) < lim2) lim2 = 448.0 / (ldexp(1.0, e1) * maxB2);
+    int e2 = isinf(lim2) ? 0 : floor_log2(lim2);
+    double lim3 = maxW3 > 0.0 ? 448.0 / maxW3 : INFINITY;
+    if (maxb3 > 0.0 && 448.0 / (ldexp(1.0, e1 + e2) * maxb3) < lim3) lim3 = 448.0 / (ldexp(1.0, e1 + e2) * maxb3);
+    int e3 = isinf(lim3) ? 0 : floor_log2(lim3);
+    e[0] = e1;
+    e[1] = e2;
+    e[2] = e3;
+    e[3] = -(e1 + e2 + e3);
+    return 0;
+}
+
+/* Three E4M3 parts of v: p0 = E4M3(v), p1 = E4M3(v - p0), p2 = E4M3(v - p0 - p1) (each
+ * difference exact in double). */
+static void e4m3_parts(double v, double* p)
+{
+    p[0] = e4m3_round(v);
+    p[1] = e4m3_round(v - p[0]);
+    p[2] = e4m3_round(v - p[0] - p[1]);
+}
+
+/* FP32 emulation of the E4M3 variant. lat16 [GH][GW][16] binary16 codes, P32 the FP32
+ * parameters (the variant's weights and scales are derived from them as the GPU does); decodes
+ * n texels idx[n] -> out[n][8]. e (optional) receives the four exponents. */
+int stf_ref_neural_decode_e4m3(const uint16_t* lat16, int GW, int GH, int R, const float* P32, const int* idx,
+                               int n, float* out, int* e_out)
+{
+    int e[4];
+    stf_ref_neural_e4m3_scales(lat16, GW, GH, P32, e);
+    if (e_out) memcpy(e_out, e, sizeof e);
+    const double s1 = ldexp(1.0, e[0]), s2 = ldexp(1.0, e[1]), s3 = ldexp(1.0, e[2]);
+    const float os = (float)ldexp(1.0, e[3]);
+    const float* W1 = P32;
+    const float* b1 = W1 + NN_H * NN_IN;
+    const float* W2 = b1 + NN_H;
+    const float* b2 = W2 + NN_H * NN_H;
+    const float* W3 = b2 + NN_H;
+    const float* b3 = W3 + NN_OUT * NN_H;
+    float w1[NN_H * NN_IN], w2[NN_H * NN_H], w3[NN_OUT * NN_H], c1[NN_H], c2[NN_H][3], c3[NN_OUT][3];
+    /* layer 1: binary16 of s1 W1, the FP32 bias s1 b1 */
+    for (int k = 0; k < NN_H * NN_IN; ++k) w1[k] = round_h((float)(s1 * (double)W1[k]));
+    for (int j = 0; j < NN_H; ++j) c1[j] = (float)(s1 * (double)b1[j]);
+    /* layers 2, 3: E4M3 of s2 W2 and s3 W3; bias parts of s2 s1 b2 and s3 s2 s1 b3 */
+    for (int k = 0; k < NN_H * NN_H; ++k) w2[k] = (float)e4m3_round(s2 * (double)W2[k]);
+    for (int k = 0; k < NN_OUT * NN_H; ++k) w3[k] = (float)e4m3_round(s3 * (double)W3[k]);
+    for (int i = 0; i < NN_H; ++i) {
+        double p[3];
+        e4m3_parts(s2 * s1 * (double)b2[i], p);
+        for (int q = 0; q < 3; ++q) c2[i][q] = (float)p[q];
+    }
+    for (int o = 0; o < NN_OUT; ++o) {
+        double p[3];
+        e4m3_parts(s3 * s2 * s1 * (double)b3[o], p);
+        for (int q = 0; q < 3; ++q) c3[o][q] = (float)p[q];
+    }
+    for (int b = 0; b < n; ++b) {
+        const int ix = idx[b] & 0xffff, iy = idx[b] >> 16;
+        int x0, x1, y0, y1;
+        double fxd, fyd;
+        latent_axis(ix, R, GW, &x0, &x1, &fxd);
+        latent_axis(iy, R, GH, &y0, &y1, &fyd);
+        const float fx = (float)fxd, fy = (float)fyd;
+        const float w00 = round_h((1.0f - fx) * (1.0f - fy)), w10 = round_h(fx * (1.0f - fy));
+        const float w01 = round_h((1.0f - fx) * fy), w11 = round_h(fx * fy);
+        const uint16_t* c00 = lat16 + ((size_t)y0 * GW + x0) * NN_LAT;
+        const uint16_t* c10 = lat16 + ((size_t)y0 * GW + x1) * NN_LAT;
+        const uint16_t* c01 = lat16 + ((size_t)y1 * GW + x0) * NN_LAT;
+        const uint16_t* c11 = lat16 + ((size_t)y1 * GW + x1) * NN_LAT;
+        float x[NN_IN];
+        for (int k = 0; k < NN_LAT; ++k) {
+            float t = mul_h(w00, h2f(c00[k]));
+            t = fma_h(w10, h2f(c10[k]), t);
+            t = fma_h(w01, h2f(c01[k]), t);
+            t = fma_h(w11, h2f(c11[k]), t);
+            x[k] = t;
+        }
+        double ph[8];
+        phase_features(ix, R, ph);
+        phase_features(iy, R, ph + 4);
+        for (int k = 0; k < 8; ++k) x[16 + k] = round_h((float)ph[k]);
+        float h1[NN_H], h2[NN_H];
+        for (int j = 0; j < NN_H; ++j) {
+            float t = 0.0f;
+            for (int k = 0; k < NN_IN; ++k) t = t + w1[j * NN_IN + k] * x[k];
+            t = t + c1[j];
+            h1[j] = (float)e4m3_round(t > 0.0f ? t : 0.0f);
+        }
+        for (int i = 0; i < NN_H; ++i) {
+            float t = 0.0f;
+            for (int j = 0; j < NN_H; ++j) t = t + w2[i * NN_H + j] * h1[j];
+            t = t + c2[i][0] + c2[i][1] + c2[i][2];
+            h2[i] = (float)e4m3_round(t > 0.0f ? t : 0.0f);
+        }
+        for (int o = 0; o < NN_OUT; ++o) {
+            float t = 0.0f;
+            for (int i = 0; i < NN_H; ++i) t = t + w3[o * NN_H + i] * h2[i];
+            t = t + c3[o][0] + c3[o][1] + c3[o][2];
+            out[(size_t)b * NN_OUT + o] = t * os;
+        }
     }
     return 0;
 }

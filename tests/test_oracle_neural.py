@@ -188,3 +188,173 @@ def test_fp16_interpolation_is_correctly_rounded():
                 for k in (1, 2, 3):
                     s = _rn_f16(w[k] * L[k] + s)
                 assert Fraction(float(got[b, j])) == s, (ix, iy, ch)
+
+
+# ----------------------------------------------------------------------------- E4M3 variant
+
+def test_e4m3_encoder_matches_torch_cast():
+    """The oracle's E4M3 rounding (nearest, ties to even) against torch's float8_e4m3fn cast on
+    random values, every exact midpoint between neighbouring codes, and the subnormal range."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8_e4m3fn in this torch")
+    rng = np.random.default_rng(21)
+    vals = [O.e4m3_value(c) for c in range(0x7f)]
+    mids = [(a + b) / 2 for a, b in zip(vals[:-1], vals[1:])]
+    xs = np.concatenate([rng.uniform(-448, 448, 4000), rng.uniform(-0.03, 0.03, 4000),
+                         np.array(mids), -np.array(mids), np.array(vals), [0.0, -0.0]]).astype(np.float32)
+    want = torch.from_numpy(xs).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    got = np.array([O.e4m3_encode(float(x)) for x in xs], np.uint8)
+    np.testing.assert_array_equal(got, want)
+    # decode of every finite code against torch
+    codes = np.arange(256, dtype=np.uint8)
+    ref = torch.from_numpy(codes).view(torch.float8_e4m3fn).float().numpy()
+    for c in range(256):
+        if c & 0x7f == 0x7f:
+            assert math.isnan(O.e4m3_value(c))
+        else:
+            assert O.e4m3_value(c) == ref[c]
+
+
+def test_e4m3_saturates_and_keeps_nan():
+    assert O.e4m3_encode(448.0) == 0x7e and O.e4m3_value(0x7e) == 448.0
+    assert O.e4m3_encode(463.9) == 0x7e and O.e4m3_encode(1e30) == 0x7e and O.e4m3_encode(-1e30) == 0xfe
+    assert O.e4m3_encode(float("nan")) & 0x7f == 0x7f
+    assert O.e4m3_encode(2.0 ** -10) == 0 and O.e4m3_encode(2.0 ** -10 * 1.0001) == 1  # tie to even, then up
+
+
+def _e4m3_first_order_bound(lat, R, P, idx, e):
+    """First-order bound on |E4M3 decode - FP64 decode| per output: u = 2^-4 relative per E4M3
+    rounding (plus half a subnormal step, 2^-10, in the scaled units), 2^-9 relative for the FP16
+    stages of layer 1, propagated through |W| with the FP64 activations."""
+    W1, b1, W2, b2, W3, b3 = [np.asarray(a, np.float64) for a in O.nn_split(np.asarray(P, np.float64))]
+    W1, W2, W3 = W1.reshape(64, 24), W2.reshape(64, 64), W3.reshape(8, 64)
+    s1, s2, s3 = 2.0 ** e[0], 2.0 ** e[1], 2.0 ** e[2]
+    u, sub = 2.0 ** -4, 2.0 ** -10
+    out = []
+    for t in idx:
+        x = O.nn_features(lat, R, int(t) & 0xffff, int(t) >> 16)
+        z1 = W1 @ x + b1
+        h1 = np.maximum(z1, 0)
+        h2 = np.maximum(W2 @ h1 + b2, 0)
+        e1 = u * h1 + sub / s1 + 2.0 ** -9 * (np.abs(W1) @ np.abs(x) + np.abs(b1))
+        e2 = (np.abs(W2) @ e1 + (u * np.abs(W2) + sub / s2) @ h1 + u ** 3 * np.abs(b2)) * (1 + u) + u * h2 + sub / (s1 * s2)
+        out.append(np.abs(W3) @ e2 + (u * np.abs(W3) + sub / s3) @ h2 + u ** 3 * np.abs(b3))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("wscale,lscale", [(0.2, 0.5), (0.6, 3.0), (0.05, 0.1)])
+def test_e4m3_emulation_within_first_order_bound_of_fp64(wscale, lscale):
+    """The E4M3 emulation stays within the first-order rounding bound of the FP64 decode of the
+    same parameters (FP16-rounded latents), for small and large activations (the power-of-two
+    scales keep them in range); and its error is well above the FP16 emulation's, so the E4M3
+    roundings do take place."""
+    rng = np.random.default_rng(int(wscale * 100 + lscale * 10))
+    gh, gw, R = 8, 8, 4
+    lat = _rand_lat(rng, gh, gw, lscale).astype(np.float16).astype(np.float64)
+    P = _rand_params(rng, wscale).astype(np.float32).astype(np.float64)
+    lat16, w16, b32 = O.nn_pack_inference(lat, P)
+    idx = np.array([(x | (y << 16)) for y in range(4 * gh) for x in range(4 * gw)], np.int32)
+    e = O.nn_e4m3_scales(lat16, P)
+    assert e[3] == -(e[0] + e[1] + e[2]) and e[0] <= 8
+    y8 = O.nn_decode_e4m3(lat16, R, P, idx).astype(np.float64)
+    y64 = O.nn_decode_f64(lat, R, P, idx)
+    y16 = O.nn_decode_f32(lat16, R, w16, b32, idx).astype(np.float64)
+    bound = _e4m3_first_order_bound(lat, R, P, idx, e)
+    err = np.abs(y8 - y64)
+    assert np.all(err <= 1.5 * bound + 1e-6), float(np.max(err / (bound + 1e-12)))
+    assert np.mean(err) > 4 * np.mean(np.abs(y16 - y64))
+
+
+def test_e4m3_scales_follow_the_activation_bound():
+    """Scaling the first layer's weights by 2^k moves log2 s1 by -k (the activation bound scales
+    with them) and leaves the decoded values unchanged up to the same output scale, since a
+    power-of-two scaling commutes with E4M3 rounding in the normal range."""
+    rng = np.random.default_rng(31)
+    gh, gw, R = 8, 8, 4
+    lat = _rand_lat(rng, gh, gw).astype(np.float16).astype(np.float64)
+    P = _rand_params(rng, 0.2).astype(np.float32).astype(np.float64)
+    lat16, _, _ = O.nn_pack_inference(lat, P)
+    e = O.nn_e4m3_scales(lat16, P)
+    Q = P.copy()
+    W1, b1, W2, b2, W3, b3 = O.nn_split(Q)
+    W1 *= 4.0
+    b1 *= 4.0
+    f = O.nn_e4m3_scales(lat16, Q)
+    assert f[0] == e[0] - 2
+    idx = np.array([(x | (y << 16)) for y in range(0, 4 * gh, 3) for x in range(0, 4 * gw, 3)], np.int32)
+    ya = O.nn_decode_e4m3(lat16, R, P, idx).astype(np.float64)
+    yb = O.nn_decode_e4m3(lat16, R, Q, idx).astype(np.float64)
+    # h1 doubles twice and W2 is unchanged, so layer 2 sees 4x inputs: s2 absorbs them only if its
+    # range limit binds; either way the decode of the scaled network is 4x in the hidden layers
+    y64a = O.nn_decode_f64(lat, R, P, idx)
+    y64b = O.nn_decode_f64(lat, R, Q, idx)
+    assert np.all(np.isfinite(ya)) and np.all(np.isfinite(yb))
+    assert np.mean(np.abs(yb - y64b)) < 0.2 * np.mean(np.abs(y64b - y64b.mean())) + 1e-3
+    assert np.mean(np.abs(ya - y64a)) < 0.2 * np.mean(np.abs(y64a - y64a.mean())) + 1e-3
+
+
+def test_e4m3_decode_of_a_sparse_network_in_closed_form():
+    """A network with one path per output (W1 reads latent 0 only, W2 and W3 diagonal) over a
+    constant latent grid: each output is then a short chain of roundings that can be written out
+    with torch's float8_e4m3fn cast (nearest even) as the E4M3 rounding: h1 = E4M3(relu(
+    fp16(s1 a) L + s1 b1)), h2 = E4M3(relu(E4M3(s2 c) h1 + parts(s1 s2 b2))), y = (E4M3(s3 d) h2
+    + parts(s1 s2 s3 b3)) / (s1 s2 s3), with FP32 sums in that order; the scale exponents are the
+    closed form of the rule for this network."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8_e4m3fn in this torch")
+
+    def q8(v):
+        return float(torch.tensor([v], dtype=torch.float64).to(torch.float32).to(torch.float8_e4m3fn).to(torch.float64)[0])
+
+    def parts(v):
+        p0 = q8(v)
+        p1 = q8(v - p0)
+        return p0, p1, q8(v - p0 - p1)
+
+    rng = np.random.default_rng(41)
+    gh, gw, R, L = 4, 4, 4, 0.75
+    lat = np.full((gh, gw, O.NN_LAT), L)
+    P = np.zeros(O.NN_PARAMS)
+    W1, b1, W2, b2, W3, b3 = O.nn_split(P)
+    a = rng.uniform(-3, 3, 64).astype(np.float16).astype(np.float64)
+    W1.reshape(64, 24)[:, 0] = a
+    b1[:] = rng.uniform(-1, 1, 64).astype(np.float32)
+    c = rng.uniform(-2, 2, 64).astype(np.float32)
+    W2.reshape(64, 64)[np.arange(64), np.arange(64)] = c
+    b2[:] = rng.uniform(-1, 1, 64).astype(np.float32)
+    d = rng.uniform(-2, 2, 8).astype(np.float32)
+    W3.reshape(8, 64)[np.arange(8), np.arange(8)] = d
+    b3[:] = rng.uniform(-1, 1, 8).astype(np.float32)
+    P = P.astype(np.float32).astype(np.float64)
+    W1, b1, W2, b2, W3, b3 = O.nn_split(P)
+    lat16, _, _ = O.nn_pack_inference(lat, P)
+    e = O.nn_e4m3_scales(lat16, P)
+    # the rule in closed form: B1_j = m |a_j| L + |b1_j|; B2_i = m^2 |c_i| B1_i + |b2_i|
+    m = 1.0625
+    B1 = m * np.abs(a) * L + np.abs(b1)
+    B2 = m * m * np.abs(c) * B1 + np.abs(b2)
+    fl = lambda v: int(np.floor(np.log2(v)))  # v is never an exact power of two here
+    e1 = min(8, fl(448 / B1.max()))
+    e2 = fl(min(448 / (2.0 ** e1 * B2.max()), 448 / np.abs(c).max()))
+    e3 = fl(min(448 / np.abs(d).max(), 448 / (2.0 ** (e1 + e2) * np.abs(b3).max())))
+    assert e == [e1, e2, e3, -(e1 + e2 + e3)]
+    s1, s2, s3 = 2.0 ** e1, 2.0 ** e2, 2.0 ** e3
+    f32 = np.float32
+    want = np.zeros(8)
+    for o in range(8):
+        z1 = f32(f32(np.float16(s1 * a[o])) * f32(L)) + f32(s1 * b1[o])
+        h1 = q8(max(float(z1), 0.0))
+        t = f32(f32(q8(s2 * c[o])) * f32(h1))
+        for p in parts(s2 * s1 * b2[o]):
+            t = f32(t + f32(p))
+        h2 = q8(max(float(t), 0.0))
+        y = f32(f32(q8(s3 * d[o])) * f32(h2))
+        for p in parts(s3 * s2 * s1 * b3[o]):
+            y = f32(y + f32(p))
+        want[o] = float(f32(y * f32(2.0 ** -(e1 + e2 + e3))))
+    idx = np.array([(x | (y << 16)) for y in range(0, 16, 5) for x in range(0, 16, 3)], np.int32)
+    got = O.nn_decode_e4m3(lat16, R, P, idx).astype(np.float64)
+    for row in got:
+        np.testing.assert_array_equal(row, want)
