@@ -364,6 +364,25 @@ stf_status stf_decoder_set_params(stf_decoder* d, const float* latent, const flo
 /* Decodes n texels (device array of packed ix | iy << 16) into out (device, n * 8 floats,
  * 16-byte aligned) with the inference kernel. Asynchronous on the library stream. */
 stf_status stf_decoder_decode(const stf_decoder* d, const int32_t* texels, int n, float* out);
+/* Inference precision of a decoder (Section 5.7 names neural texture decompression as the costly
+ * decode that stochastic filtering amortises; the FP8 option is this library's, as the compressed
+ * format is not given):
+ *   STF_NN_FP16 (the default) as described above;
+ *   STF_NN_E4M3 layers 2 and 3 as OCP E4M3 tensor-core products (kind::f8f6f4, FP32 accumulation):
+ *               W2, W3 and both hidden activations rounded to E4M3 (nearest even, saturating,
+ *               ReLU before the rounding), each bias of those layers as three E4M3 parts; layer 1
+ *               stays FP16. Power-of-two scalings s1 (layer-1 weights and bias), s2 (W2), s3 (W3),
+ *               chosen from a first-order bound of the activations (max |latent| per channel, the
+ *               parameters' absolute row sums) so that no weight or activation exceeds 448, keep
+ *               the values in range; outputs are multiplied by 1 / (s1 s2 s3).
+ * The choice holds for stf_decoder_decode and for every texture made from the decoder, and is
+ * kept across training and stf_decoder_set_params (the scalings are recomputed whenever the
+ * inference copy is refreshed); a loaded checkpoint starts in FP16. exponents (host, may be
+ * NULL) receives log2 s1, log2 s2, log2 s3 and log2 of the output scale (zeros for FP16).
+ * Synchronous (it reads the latent grid back to find the bound). Must not overlap a render or
+ * decode that uses the decoder. STF_ERR_INVALID_ARG for another format. */
+enum { STF_NN_FP16 = 0, STF_NN_E4M3 = 1 };
+stf_status stf_decoder_set_inference(stf_decoder* d, int format, int* exponents);
 /* Configuration and number of completed training steps. */
 stf_status stf_decoder_info(const stf_decoder* d, stf_decoder_config* cfg, long long* step);
 /* Checkpoints: parameters, Adam moments, step, configuration and a CRC-32 of the file. load

@@ -19,8 +19,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libstf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC,
-              "--expt-relaxed-constexpr"]
+# host code without floating-point contraction (the E4M3 scale rule's FP64 sums must not turn into
+# fused multiply-adds on hosts that have them)
+NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "-I" + INCLUDE, "-I" + CSRC, "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:

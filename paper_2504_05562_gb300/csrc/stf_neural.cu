@@ -5,9 +5,12 @@
 // over fixed chunks of the batch in a fixed order, and latent gradients are accumulated as 64-bit
 // fixed-point integers, whose atomic sums do not depend on the order of the additions.
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -316,6 +319,52 @@ __global__ void k_nn_export(const float* P, const float* lat, long long nlat, __
     }
 }
 
+// The E4M3 variant's image (see kNnK8): layer 1 as k_nn_export with W1 and b1 scaled by
+// s1 = 2^e1, then W2 / W3 as E4M3 of s2 W2 / s3 W3 and the three E4M3 parts of s1 s2 b2 and
+// s1 s2 s3 b3 in K 64 .. 66 (every scaling exact, every difference of the parts exact).
+__device__ __forceinline__ unsigned char nn_e4m3(float v) { return (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3); }
+__device__ __forceinline__ float nn_e4m3_value(unsigned char c)
+{
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)c, __NV_E4M3)));
+}
+
+__global__ void k_nn_export_e4m3(const float* P, unsigned char* img, int e1, int e2, int e3)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float s1 = ldexpf(1.0f, e1), s2 = ldexpf(1.0f, e2), s3 = ldexpf(1.0f, e3);
+    constexpr int n1 = 64 * kNnK1, n2 = 64 * kNnK8, n3 = 16 * kNnK8;
+    if (i < n1) {
+        const int r = i / kNnK1, k = i % kNnK1;
+        const float b = s1 * P[ob1 + r];
+        __half val = __float2half_rn(0.0f);
+        if (k < kNnIn) val = __float2half_rn(s1 * P[oW1 + r * kNnIn + k]);
+        else if (k == kNnIn) val = __float2half_rn(b);
+        else if (k == kNnIn + 1) val = __float2half_rn(b - __half2float(__float2half_rn(b)));
+        *reinterpret_cast<__half*>(img + (r / 8) * (kNnK1 / 8) * 128 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2) = val;
+    } else if (i < n1 + n2 + n3) {
+        int j = i - n1, base = kNnB1Bytes, rows = kNnH;
+        const float* Wm = P + oW2;
+        const float* bv = P + ob2;
+        float sw = s2, sb = s1 * s2;
+        if (j >= n2) { j -= n2; base += kNnB2Bytes8; rows = kNnOut; Wm = P + oW3; bv = P + ob3; sw = s3; sb = s1 * s2 * s3; }
+        const int r = j / kNnK8, k = j % kNnK8;
+        unsigned char val = 0;
+        if (r < rows) {
+            if (k < kNnH) val = nn_e4m3(sw * Wm[r * kNnH + k]);
+            else if (k < kNnH + 3) {
+                float v = sb * bv[r];
+                unsigned char q = nn_e4m3(v);
+                for (int t = kNnH; t < k; ++t) {  // the part k - 64 of v: peel the earlier parts
+                    v -= nn_e4m3_value(q);
+                    q = nn_e4m3(v);
+                }
+                val = q;
+            }
+        }
+        img[base + (r / 8) * (kNnK8 / 16) * 128 + (k / 16) * 128 + (r % 8) * 16 + (k % 16)] = val;
+    }
+}
+
 // Decodes a list of texels (packed ix | iy << 16) through the decode pipeline: persistent blocks,
 // kNnClients texels per round (a tail round decodes fewer rows).
 __global__ void __launch_bounds__(kNnPipeThreads, 2) k_nn_decode_list(const NeuralDev* nd, const int* idx, int n, int W,
@@ -383,6 +432,8 @@ struct stf_decoder {
     __half* lat16 = nullptr;
     __half* wimg = nullptr;
     NeuralDev* dev = nullptr;  // device copy of the inference parameter block
+    int infer_fmt = 0;         // STF_NN_FP16 or STF_NN_E4M3
+    int e8[4] = {0, 0, 0, 0};  // E4M3 variant: log2 s1, s2, s3 and of the output scale
     float feat[16][4];         // FP32 phase features (training)
     // per-batch scratch
     int cap = 0;
@@ -471,12 +522,93 @@ stf_status ensure_scratch(stf_decoder* d, int n)
     return STF_OK;
 }
 
+// floor(log2(v)) of a positive v, exactly.
+int floor_log2(double v)
+{
+    int e;
+    (void)std::frexp(v, &e);
+    return e - 1;
+}
+
+// The E4M3 variant's power-of-two exponents from the FP16 latent grid and the FP32 parameters,
+// every sum in FP64 in index order (m = 1.0625, one E4M3 rounding):
+//   xmax_k  max |latent k| over the grid (k < 16), 1 for the position features;
+//   B1_j    m sum_k |W1_jk| xmax_k + |b1_j|  (bounds |h1_j|),  B2_i  m^2 sum_j |W2_ij| B1_j + |b2_i|;
+//   e1      floor(log2(448 / max B1)), at most 8;
+//   e2      floor(log2(min(448 / (2^e1 max B2), 448 / max |W2|)));
+//   e3      floor(log2(min(448 / max |W3|, 448 / (2^(e1 + e2) max |b3|))));
+// e[3] = -(e1 + e2 + e3), the output scale's exponent. No activation or weight then exceeds 448.
+void e4m3_exponents(const std::vector<__half>& lat16, const std::vector<float>& P, int (&e)[4])
+{
+    const double m = 1.0625;
+    double xmax[kNnIn];
+    for (int k = 0; k < kNnIn; ++k) xmax[k] = k < kNnLat ? 0.0 : 1.0;
+    for (size_t c = 0; c + kNnLat <= lat16.size(); c += kNnLat)
+        for (int k = 0; k < kNnLat; ++k) xmax[k] = std::max(xmax[k], std::fabs((double)__half2float(lat16[c + k])));
+    double B1[kNnH], maxB1 = 0.0, maxB2 = 0.0, maxW2 = 0.0, maxW3 = 0.0, maxb3 = 0.0;
+    for (int j = 0; j < kNnH; ++j) {
+        double t = 0.0;
+        for (int k = 0; k < kNnIn; ++k) t += std::fabs((double)P[oW1 + j * kNnIn + k]) * xmax[k];
+        B1[j] = m * t + std::fabs((double)P[ob1 + j]);
+        maxB1 = std::max(maxB1, B1[j]);
+    }
+    for (int i = 0; i < kNnH; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < kNnH; ++j) {
+            const double w = std::fabs((double)P[oW2 + i * kNnH + j]);
+            t += w * B1[j];
+            maxW2 = std::max(maxW2, w);
+        }
+        maxB2 = std::max(maxB2, m * m * t + std::fabs((double)P[ob2 + i]));
+    }
+    for (int k = 0; k < kNnOut * kNnH; ++k) maxW3 = std::max(maxW3, std::fabs((double)P[oW3 + k]));
+    for (int o = 0; o < kNnOut; ++o) maxb3 = std::max(maxb3, std::fabs((double)P[ob3 + o]));
+    int e1 = maxB1 > 0.0 ? floor_log2(448.0 / maxB1) : 8;
+    if (e1 > 8) e1 = 8;
+    double lim2 = maxW2 > 0.0 ? 448.0 / maxW2 : INFINITY;
+    if (maxB2 > 0.0) lim2 = std::min(lim2, 448.0 / (std::ldexp(1.0, e1) * maxB2));
+    const int e2 = std::isinf(lim2) ? 0 : floor_log2(lim2);
+    double lim3 = maxW3 > 0.0 ? 448.0 / maxW3 : INFINITY;
+    if (maxb3 > 0.0) lim3 = std::min(lim3, 448.0 / (std::ldexp(1.0, e1 + e2) * maxb3));
+    const int e3 = std::isinf(lim3) ? 0 : floor_log2(lim3);
+    e[0] = e1;
+    e[1] = e2;
+    e[2] = e3;
+    e[3] = -(e1 + e2 + e3);
+}
+
+// The inference copy of the parameters: FP16 latents, and the weight image of the decoder's
+// inference format (for the E4M3 variant, its exponents from the exported latents and the
+// current parameters), then the format fields of the device parameter block.
 stf_status export_inference(stf_decoder* d, cudaStream_t s)
 {
     const long long n = d->nlat > kNnImgBytes / 2 ? d->nlat : kNnImgBytes / 2;
     k_nn_export<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d->P, d->lat, d->nlat, d->lat16, d->wimg);
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? STF_OK : stf_cuda_fail(e, "export kernel");
+    if (e != cudaSuccess) return stf_cuda_fail(e, "export kernel");
+    int fp8 = 0;
+    float os = 1.0f;
+    if (d->infer_fmt == STF_NN_E4M3) {
+        std::vector<__half> lat((size_t)d->nlat);
+        std::vector<float> P(kNnParams);
+        if ((e = cudaMemcpyAsync(lat.data(), d->lat16, lat.size() * sizeof(__half), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(P.data(), d->P, P.size() * sizeof(float), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return stf_cuda_fail(e, "reading the parameters for the E4M3 scales");
+        e4m3_exponents(lat, P, d->e8);
+        constexpr int nimg = 64 * kNnK1 + 64 * kNnK8 + 16 * kNnK8;
+        k_nn_export_e4m3<<<(nimg + 255) / 256, 256, 0, s>>>(d->P, reinterpret_cast<unsigned char*>(d->wimg), d->e8[0],
+                                                            d->e8[1], d->e8[2]);
+        if ((e = cudaGetLastError()) != cudaSuccess) return stf_cuda_fail(e, "E4M3 export kernel");
+        fp8 = 1;
+        os = std::ldexp(1.0f, d->e8[3]);
+    }
+    struct { int fp8; float out_scale; } f{fp8, os};
+    static_assert(offsetof(NeuralDev, out_scale) == offsetof(NeuralDev, fp8) + sizeof(int), "adjacent fields");
+    if ((e = cudaMemcpyAsync(reinterpret_cast<char*>(d->dev) + offsetof(NeuralDev, fp8), &f, sizeof f, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return stf_cuda_fail(e, "inference format");
+    return STF_OK;
 }
 
 stf_status target_args(const stf_decoder* d, const stf_texture* t)
@@ -673,6 +805,19 @@ extern "C" stf_status stf_decoder_decode(const stf_decoder* d, const int32_t* te
     k_nn_decode_list<<<blocks, kNnPipeThreads, sizeof(NnPipeSmem), stf_stream()>>>(d->dev, texels, n, d->cfg.tex_w, d->cfg.tex_h, out, flags);
     e = cudaGetLastError();
     return e == cudaSuccess ? STF_OK : stf_cuda_fail(e, "decode kernel");
+}
+
+extern "C" stf_status stf_decoder_set_inference(stf_decoder* d, int format, int* exponents)
+{
+    if (!d) return stf_fail(STF_ERR_INVALID_ARG, "null decoder");
+    if (format != STF_NN_FP16 && format != STF_NN_E4M3)
+        return stf_fail(STF_ERR_INVALID_ARG, "inference format %d (STF_NN_FP16 or STF_NN_E4M3)", format);
+    d->infer_fmt = format;
+    stf_status st = export_inference(d, stf_stream());
+    if (st != STF_OK) return st;
+    if (exponents)
+        for (int k = 0; k < 4; ++k) exponents[k] = format == STF_NN_E4M3 ? d->e8[k] : 0;
+    return STF_OK;
 }
 
 extern "C" stf_status stf_decoder_info(const stf_decoder* d, stf_decoder_config* cfg, long long* step)

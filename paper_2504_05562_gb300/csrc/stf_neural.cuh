@@ -37,6 +37,17 @@ constexpr int kNnB2Bytes = 64 * kNnK2 * 2;  // W2: N = 64 x K = 80
 constexpr int kNnB3Bytes = 16 * kNnK2 * 2;  // W3: N = 16 (8 outputs + zero rows) x K = 80
 constexpr int kNnImgBytes = kNnB1Bytes + kNnB2Bytes + kNnB3Bytes;  // 16896
 
+// E4M3 variant of the image (the FP8 inference precision the c4 workload allows): layer 1 stays
+// FP16 with its weights and bias scaled by s1; layers 2 and 3 are OCP E4M3 kind::f8f6f4
+// products, W2 and W3 scaled by s2 and s3, each bias split into three E4M3 parts (K 64 .. 66)
+// against activation columns of 1, so a row is K = 96 bytes (three K steps of 32). The hidden
+// activations are rounded to E4M3 (ReLU, satfinite) in the epilogue; the outputs are scaled back
+// by 1 / (s1 s2 s3). s1, s2, s3 are powers of two from a first-order bound of the activations
+// (stf_decoder_set_inference), so that neither weights nor activations saturate.
+constexpr int kNnK8 = 96;
+constexpr int kNnB2Bytes8 = 64 * kNnK8, kNnB3Bytes8 = 16 * kNnK8;
+static_assert(kNnB1Bytes + kNnB2Bytes8 + kNnB3Bytes8 <= kNnImgBytes, "the E4M3 image fits the FP16 one's space");
+
 // Device parameter block of a decoder's inference copy.
 struct NeuralDev {
     const uint4* lat16;   // [gh][gw][2]: 16 FP16 latents per cell
@@ -44,6 +55,8 @@ struct NeuralDev {
     float inv_r;          // 1 / R (exact)
     uint2 feat[16];       // phase p: (sin, cos)(2 pi phi) and (sin, cos)(4 pi phi) as half2 pairs
     const uint4* wimg;    // the three layers (weights and biases) as tensor-core B operands
+    int fp8;              // 1: the E4M3 variant (layers 2 and 3 as FP8 products, see below)
+    float out_scale;      // E4M3 variant: 1 / (s1 s2 s3), exact; 1 otherwise
 };
 
 // Bilinear position along one latent axis: lower cell, upper cell (both clamped) and fraction.
@@ -159,6 +172,15 @@ __device__ __forceinline__ void nn_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint
         :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
+// The same with kind::f8f6f4 (A and B E4M3: the type fields of the instruction descriptor are 0).
+__device__ __forceinline__ void nn_mma_ts_f8(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc, uint32_t accum)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n"
+        :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
 __device__ __forceinline__ void nn_commit(uint32_t mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
@@ -217,6 +239,18 @@ __device__ __forceinline__ uint32_t relu_pack_h2(float lo, float hi)
     return d;
 }
 
+// ReLU, then round four values to E4M3 (nearest even, saturating), packed low to high.
+__device__ __forceinline__ uint32_t relu_pack_e4m3x4(float a, float b, float c, float d)
+{
+    uint32_t r;
+    asm("{\n\t.reg .b16 lo, hi;\n\t"
+        "cvt.rn.satfinite.relu.e4m3x2.f32 lo, %2, %1;\n\t"
+        "cvt.rn.satfinite.relu.e4m3x2.f32 hi, %4, %3;\n\t"
+        "mov.b32 %0, {lo, hi};\n}\n"
+        : "=r"(r) : "f"(a), "f"(b), "f"(c), "f"(d));
+    return r;
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {
     asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" :: "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
@@ -271,6 +305,8 @@ struct NnPipeSmem {
     unsigned long long in_full[2], out_full[2], mma[2], mma_out[2], epi[2];
     uint32_t tmem;
     int more[2];             // 1: the round in this slot carries rows, 0: the clients are done
+    int fp8;                 // the decoder's E4M3 variant (NeuralDev::fp8)
+    float out_scale;         // and its output scale
 };
 
 // Bounded mbarrier waits of one thread.
@@ -302,6 +338,8 @@ __device__ __forceinline__ void nn_pipe_setup(NnPipeSmem& sm, const NeuralDev* n
     uint4* dst = reinterpret_cast<uint4*>(sm.b);
     for (int i = threadIdx.x; i < kNnImgBytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
     if (threadIdx.x == 0) {
+        sm.fp8 = nd->fp8;
+        sm.out_scale = nd->out_scale;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.in_full[0])), "r"(kNnClients) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.in_full[1])), "r"(kNnClients) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&sm.epi[0])), "r"(128) : "memory");
@@ -435,6 +473,27 @@ __device__ __forceinline__ void nn_hidden_epilogue(uint32_t t_acc, uint32_t t_hi
     tmem_wait_st();
 }
 
+// E4M3 variant: the 64 activations as 16 columns of four E4M3 each (K order low to high bytes).
+__device__ __forceinline__ void nn_hidden_epilogue_e4m3(uint32_t t_acc, uint32_t t_hid)
+{
+    float v[64];
+    tmem_ld64(t_acc, v);
+    uint32_t h[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) h[j] = relu_pack_e4m3x4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    tmem_st16(t_hid, h);
+    tmem_wait_st();
+}
+
+// One layer's three E4M3 products of one tile (K = 96: A from TMEM, 8 columns per K step of 32;
+// B advanced by two 128-byte core matrices).
+__device__ __forceinline__ void nn_issue_tile_f8(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc, uint32_t mbar)
+{
+#pragma unroll
+    for (int s = 0; s < kNnK8 / 32; ++s) nn_mma_ts_f8(d_tmem, a_tmem + 8 * s, b_desc + 16 * s, idesc, s > 0 ? 1u : 0u);
+    nn_commit(mbar);
+}
+
 // One layer's K / 16 products of one tile, issued by one thread and committed to the tile's
 // barrier. A from shared memory: a_desc / b_desc describe the first K step and a step advances
 // both by 256 bytes (16 in the descriptors' address field).
@@ -462,15 +521,18 @@ __device__ __forceinline__ void nn_issue_tile_ts(uint32_t d_tmem, uint32_t a_tme
 // elsewhere (kNnOutCol), so the next round starts without waiting for round r's outputs.
 // Commits: mma[mt] completes twice per round (layers 1, 2), mma_out[mt] once (layer 3); neither
 // runs more than one phase ahead of the epilogue, which consumes them in issue order.
-template <bool TEST>
+template <bool TEST, bool F8>
 __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
 {
     const uint32_t tmem = sm.tmem, b = smem_u32(sm.b);
     const uint32_t bar[2] = {smem_u32(&sm.mma[0]), smem_u32(&sm.mma[1])};
     const uint32_t bar_out[2] = {smem_u32(&sm.mma_out[0]), smem_u32(&sm.mma_out[1])};
     constexpr uint32_t sbo1 = kNnK1 / 8 * 128, sbo2 = kNnK2 / 8 * 128;
-    const uint64_t b1 = nn_sdesc(b, 128, sbo1), b2 = nn_sdesc(b + kNnB1Bytes, 128, sbo2);
-    const uint64_t b3 = nn_sdesc(b + kNnB1Bytes + kNnB2Bytes, 128, sbo2);
+    constexpr bool f8 = F8;
+    constexpr uint32_t sbo8 = kNnK8 / 16 * 128;
+    const uint64_t b1 = nn_sdesc(b, 128, sbo1);
+    const uint64_t b2 = f8 ? nn_sdesc(b + kNnB1Bytes, 128, sbo8) : nn_sdesc(b + kNnB1Bytes, 128, sbo2);
+    const uint64_t b3 = f8 ? nn_sdesc(b + kNnB1Bytes + kNnB2Bytes8, 128, sbo8) : nn_sdesc(b + kNnB1Bytes + kNnB2Bytes, 128, sbo2);
     const bool leader = (threadIdx.x & 31) == 0;
     NnWaiter w{flags, 0};
     uint32_t eph[2] = {0u, 0u}, c12 = 0, c3 = 0;  // commits per tile on mma[] and on mma_out[]
@@ -502,8 +564,13 @@ __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
                 tc_fence_after();
                 if (leader) {
                     const uint32_t a = tmem + kNnHidCol + mt * kNnHidCols;
-                    if (layer == 2) nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b2, nn_idesc(64), bar[mt]);
-                    else nn_issue_tile_ts<kNnK2>(tmem + kNnOutCol + mt * 16, a, b3, nn_idesc(16), bar_out[mt]);
+                    if constexpr (F8) {
+                        if (layer == 2) nn_issue_tile_f8(tmem + mt * 64, a, b2, nn_idesc(64), bar[mt]);
+                        else nn_issue_tile_f8(tmem + kNnOutCol + mt * 16, a, b3, nn_idesc(16), bar_out[mt]);
+                    } else {
+                        if (layer == 2) nn_issue_tile_ts<kNnK2>(tmem + mt * 64, a, b2, nn_idesc(64), bar[mt]);
+                        else nn_issue_tile_ts<kNnK2>(tmem + kNnOutCol + mt * 16, a, b3, nn_idesc(16), bar_out[mt]);
+                    }
                 }
                 __syncwarp();
             }
@@ -520,17 +587,20 @@ __device__ __forceinline__ void nn_mma_role(NnPipeSmem& sm, int* flags)
 
 // The epilogue warpgroup: per round and tile, turn layer 1 and 2 accumulators into the next
 // layer's FP16 activations (in TMEM), then write the layer-3 outputs to shared memory.
-template <bool TEST>
+template <bool TEST, bool F8>
 __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
 {
     // row within a tile = TMEM lane: a warp reaches the 32 lanes of quarter (warp id mod 4)
     const int m = (((int)threadIdx.x >> 5) & 3) * 32 + ((int)threadIdx.x & 31);
     const uint32_t t_lane = sm.tmem + ((uint32_t)(m & ~31) << 16);
-    // the constant bias columns of the hidden operands: K 64, 65 = 1, K 66 .. 79 = 0
+    // the constant bias columns of the hidden operands: K 64, 65 = 1, K 66 .. 79 = 0 (FP16, from
+    // column 32); E4M3 variant: K 64 .. 66 = 1, K 67 .. 95 = 0 (from column 16)
+    constexpr bool f8 = F8;
     {
-        const uint32_t c[8] = {0x3c003c00u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-        tmem_st8(t_lane + kNnHidCol + 32, c);
-        tmem_st8(t_lane + kNnHidCol + kNnHidCols + 32, c);
+        const uint32_t c[8] = {f8 ? 0x00383838u : 0x3c003c00u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        const uint32_t at = f8 ? 16u : 32u;
+        tmem_st8(t_lane + kNnHidCol + at, c);
+        tmem_st8(t_lane + kNnHidCol + kNnHidCols + at, c);
         tmem_wait_st();
     }
     NnWaiter w{flags, 0};
@@ -557,8 +627,10 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
                 tile_wait(mt);
                 // after a timeout (test switch) no TMEM access, but the arrivals go on so the other
                 // roles drain
-                if (!(TEST && guard && __any_sync(0xffffffffu, w.dead)))
-                    nn_hidden_epilogue(t_lane + mt * 64, t_lane + kNnHidCol + mt * kNnHidCols);
+                if (!(TEST && guard && __any_sync(0xffffffffu, w.dead))) {
+                    if constexpr (F8) nn_hidden_epilogue_e4m3(t_lane + mt * 64, t_lane + kNnHidCol + mt * kNnHidCols);
+                    else nn_hidden_epilogue(t_lane + mt * 64, t_lane + kNnHidCol + mt * kNnHidCols);
+                }
                 tc_fence_before();
                 nn_arrive(smem_u32(&sm.epi[mt]));
             }
@@ -578,6 +650,11 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
             } else {
                 tmem_ld8(t_lane + kNnOutCol + mt * 16, o);
             }
+            if constexpr (F8) {
+                const float os = sm.out_scale;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) o[c] *= os;
+            }
             sm.out[slot][0][mt * 128 + m] = make_float4(o[0], o[1], o[2], o[3]);
             sm.out[slot][1][mt * 128 + m] = make_float4(o[4], o[5], o[6], o[7]);
         }
@@ -591,8 +668,14 @@ __device__ __forceinline__ void nn_epilogue_role(NnPipeSmem& sm, int* flags)
 template <bool TEST = false>
 __device__ __forceinline__ void nn_decode_role(NnPipeSmem& sm, int* flags)
 {
-    if ((threadIdx.x >> 5) == kNnMmaWarp) nn_mma_role<TEST>(sm, flags);
-    else nn_epilogue_role<TEST>(sm, flags);
+    // the decoder's format is fixed for the launch: each role is compiled for both and chosen once
+    if ((threadIdx.x >> 5) == kNnMmaWarp) {
+        if (sm.fp8) nn_mma_role<TEST, true>(sm, flags);
+        else nn_mma_role<TEST, false>(sm, flags);
+    } else {
+        if (sm.fp8) nn_epilogue_role<TEST, true>(sm, flags);
+        else nn_epilogue_role<TEST, false>(sm, flags);
+    }
 }
 
 }  // namespace stf

@@ -32,14 +32,18 @@ def _bind(L):
     L.stf_decoder_save.argtypes = [vp, C.c_char_p]
     L.stf_decoder_load.argtypes = [C.c_char_p, C.POINTER(C.c_void_p)]
     L.stf_decoder_destroy.argtypes = [vp]
+    L.stf_decoder_set_inference.argtypes = [vp, ip, vp]
     for n in ("stf_decoder_create", "stf_decoder_train", "stf_decoder_gradients", "stf_decoder_get_params",
               "stf_decoder_set_params", "stf_decoder_decode", "stf_decoder_info", "stf_decoder_save",
-              "stf_decoder_load", "stf_decoder_destroy"):
+              "stf_decoder_load", "stf_decoder_destroy", "stf_decoder_set_inference"):
         getattr(L, n).restype = C.c_int
 
 
 def _np_ptr(a):
     return a.ctypes.data
+
+
+INFER_FP16, INFER_E4M3 = 0, 1
 
 
 class Decoder:
@@ -94,6 +98,15 @@ class Decoder:
         P = np.ascontiguousarray(P, np.float32)
         assert lat.size == self.latent_w * self.latent_h * NN_LAT and P.size == NN_PARAMS
         stf._check(stf.load().stf_decoder_set_params(self.handle, _np_ptr(lat), _np_ptr(P)))
+
+    def set_inference(self, fmt):
+        """Inference precision: "fp16" (default) or "e4m3" (FP8 products for layers 2 and 3).
+        Returns the exponents (log2 s1, log2 s2, log2 s3, log2 output scale) of the E4M3 scalings."""
+        import numpy as np
+        code = {"fp16": INFER_FP16, "e4m3": INFER_E4M3}[fmt]
+        e = np.zeros(4, np.int32)
+        stf._check(stf.load().stf_decoder_set_inference(self.handle, code, _np_ptr(e)))
+        return [int(v) for v in e]
 
     def decode(self, texels):
         """texels: CUDA int32 tensor of packed ix | iy << 16 -> CUDA float32 tensor [n, 8]."""

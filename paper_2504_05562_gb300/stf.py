@@ -59,7 +59,7 @@ EXPORTS = ("stf_create_texture", "stf_render_views", "stf_destroy", "stf_set_str
            "stf_decoder_save", "stf_decoder_load", "stf_decoder_destroy", "stf_set_option", "stf_get_stat",
            "stf_autotune", "stf_view_config", "stf_autotune_save", "stf_autotune_load", "stf_autotune_clear",
            "stf_render_views_noalloc", "stf_sparse_footprints", "stf_set_sparse_footprints",
-           "stf_blue_noise_masks", "stf_set_blue_noise", "stf_update_texture")
+           "stf_blue_noise_masks", "stf_set_blue_noise", "stf_update_texture", "stf_decoder_set_inference")
 NOALLOC_MAX_VIEWS, NOALLOC_MAX_ITEMS = 224, 262144
 OPT_BATCH_GRAPHS, OPT_PIPELINE_BLOCKS, OPT_TEST_DECODE_STALL, OPT_PAIRED_PIXELS, OPT_TMA_STAGE = 1, 2, 3, 4, 5
 STAT_GRAPH_BUILDS, STAT_GRAPH_REPLAYS = 1, 2
