@@ -576,6 +576,27 @@ def neural_extra(a, stf, torch, W, view, flush):
         res[name]["psnr_db_vs_uncompressed_full"] = psnr(torch, imgs[name], ref)
         if name != "full":
             res[name]["psnr_db_vs_neural_full"] = psnr(torch, imgs[name], imgs["full"])
+    # the same trained decoder in its E4M3 inference variant (FP8 products for layers 2 and 3)
+    e8 = dec.set_inference("e4m3")
+    se8 = 0.0
+    for c0 in range(0, n, 1 << 20):
+        idx = torch.arange(c0, min(n, c0 + (1 << 20)), dtype=torch.int64, device="cuda")
+        packed = ((idx % a.tex) | ((idx // a.tex) << 16)).to(torch.int32)
+        d = dec.decode(packed)
+        se8 += float(((d.double() - srct[c0:c0 + d.shape[0]].double()) ** 2).sum())
+    res8 = {}
+    for name in ("one_tap", a.mode, "full"):
+        m = MODES[name]
+        cv = stf.make_view(dict(view, frame=0), ntex, out)
+        tt = time_fn(torch, lambda: stf.render_views([cv], stf.FILTER_PER_VIEW, m, 0), max(5, a.steps // 2), 3, flush)
+        img = torch.empty_like(out)
+        stf.render_views([stf.make_view(dict(view, frame=0), ntex, img)], stf.FILTER_PER_VIEW, m, 0)
+        torch.cuda.synchronize()
+        res8[name] = {"ms_median": statistics.median(tt), "gpix_s": a.width * a.height / (statistics.median(tt) * 1e-3) / 1e9,
+                      "psnr_db_vs_uncompressed_full": psnr(torch, img, ref)}
+    dec.set_inference("fp16")
+    e4m3 = {"exponents_log2_s1_s2_s3_out": e8, "decode_psnr_db": 10 * np.log10(1.0 / (se8 / (n * 8))), "modes": res8,
+            "reuse_time_over_one_tap": res8[a.mode]["ms_median"] / res8["one_tap"]["ms_median"]}
     flops_px = 2 * (24 * 64 + 64 * 64 + 64 * 8)  # the MLP's algorithmic flops per decode
     ms1 = res["one_tap"]["ms_median"]
     return {"workload": "c4-4k: %dx%d, %d^2 material, %d^2x16 FP16 latents + MLP 24-64-64-8, %s"
@@ -588,7 +609,7 @@ def neural_extra(a, stf, torch, W, view, flush):
             "full_time_over_one_tap": res["full"]["ms_median"] / ms1,
             "decode_tflops_one_tap": a.width * a.height * flops_px / (ms1 * 1e-3) / 1e12,
             "decode_flops_per_texel": {"algorithmic": flops_px, "executed": 2 * (32 * 64 + 80 * 64 + 80 * 16)},
-            "tensor_peak_tflops_bf16_measured": load_peaks().get("bf16_tflops")}, dec
+            "tensor_peak_tflops_bf16_measured": load_peaks().get("bf16_tflops"), "e4m3": e4m3}, dec
 
 
 def batch_extra(a, stf, torch, W, tex, flush):
@@ -673,6 +694,12 @@ def precision_vs_oracle(a, stf, torch, W, dec=None):
         err = np.abs(got - ref)
         res["neural_decode"] = {"max_abs": float(err.max()), "psnr_db": float(10 * np.log10(1.0 / np.mean(err ** 2))),
                                 "texels": int(idx.size), "reference": "oracle FP64 decoder, same parameters"}
+        dec.set_inference("e4m3")
+        got8 = dec.decode(torch.from_numpy(idx).cuda()).cpu().numpy().astype(np.float64)
+        dec.set_inference("fp16")
+        err8 = np.abs(got8 - ref)
+        res["neural_decode_e4m3"] = {"max_abs": float(err8.max()), "psnr_db": float(10 * np.log10(1.0 / np.mean(err8 ** 2))),
+                                     "texels": int(idx.size), "reference": "oracle FP64 decoder, same parameters"}
     res["seconds"] = time.perf_counter() - t0
     return res
 
