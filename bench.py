@@ -57,16 +57,19 @@ def parse():
     p.add_argument("--neural-steps", type=int, default=2000)
     p.add_argument("--workload", default="c3", choices=["c3", "c4"],
                    help="c3: FP16 material (default); c4: the same frame over the neural material")
+    p.add_argument("--neural-format", default="fp16", choices=["fp16", "e4m3"],
+                   help="c4: the decoder's inference precision (e4m3: FP8 products for layers 2 and 3)")
     return p.parse_args()
 
 
 def workload_config(a):
     if getattr(a, "workload", "c3") == "c4":
         return {"workload": "c4-4k: %dx%d screen-aligned 4x over a %dx%d neural material (%dx%dx16 FP16 latents, "
-                            "MLP 24-64-64-8 on tensor cores, %d training steps), %s, %s footprint, 8x4 tiles, "
-                            "Lambert+GGX" % (a.width, a.height, a.tex, a.tex, a.tex // 4, a.tex // 4, a.neural_steps,
-                                             a.filter, a.mode),
-                "screen": [a.width, a.height], "texture": [a.tex, a.tex, 8], "format": "neural", "filter": a.filter,
+                            "MLP 24-64-64-8 on tensor cores, %s inference, %d training steps), %s, %s footprint, 8x4 tiles, "
+                            "Lambert+GGX" % (a.width, a.height, a.tex, a.tex, a.tex // 4, a.tex // 4,
+                                             getattr(a, "neural_format", "fp16").upper(), a.neural_steps, a.filter, a.mode),
+                "screen": [a.width, a.height], "texture": [a.tex, a.tex, 8], "format": "neural",
+                "inference": getattr(a, "neural_format", "fp16"), "filter": a.filter,
                 "mode": a.mode, "tile": [8, 4], "magnification": 4.0, "shading": "lambert+ggx",
                 "l2": "flushed (256 MB memset) before every timed launch"}
     return {"workload": "c3-4k: %dx%d screen-aligned 4x over %dx%d 8-ch %s material, %s, %s footprint, 8x4 tiles, "
@@ -329,6 +332,7 @@ def run_ours(a):
         decoder = neural.Decoder(a.tex, a.tex, a.tex // 4, a.tex // 4, batch=65536, seed=0)
         if a.neural_steps:
             decoder.train(stf.Texture(W.make_material(src, W.FP32)), a.neural_steps)
+        decoder.set_inference(a.neural_format)
         tex = decoder.texture()
     out = torch.empty((a.height, a.width, 4), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
