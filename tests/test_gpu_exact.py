@@ -5,9 +5,10 @@ full bilinear filter (where its footprint's samples cover its filter's texels, f
 sampled indices by exact_support.py) or the plain estimate of the same sharing mode; and the render
 must match the oracle's exact-filtering render within the colour tolerance. Also for the neural
 material, the multi-view batch, and every tile shape. Unshaded colours are the channels and compare
-bit for bit too; shaded colours compare within 1e-5 relative, because exact filtering renders one
-pixel per thread while the full filter and the plain estimate take the paired path, whose packed
-shading the compiler may contract differently (an ulp).
+bit for bit too; shaded colours compare within 1e-5 relative, because some of the compared renders
+run one pixel per thread (the neural material, tile shapes whose pixel pairs do not share a
+window) and others the paired path, whose packed shading the compiler may contract differently
+(an ulp).
 """
 import numpy as np
 import pytest
