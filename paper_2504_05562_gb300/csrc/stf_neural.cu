@@ -812,9 +812,13 @@ extern "C" stf_status stf_decoder_set_inference(stf_decoder* d, int format, int*
     if (!d) return stf_fail(STF_ERR_INVALID_ARG, "null decoder");
     if (format != STF_NN_FP16 && format != STF_NN_E4M3)
         return stf_fail(STF_ERR_INVALID_ARG, "inference format %d (STF_NN_FP16 or STF_NN_E4M3)", format);
+    const int before = d->infer_fmt;
     d->infer_fmt = format;
     stf_status st = export_inference(d, stf_stream());
-    if (st != STF_OK) return st;
+    if (st != STF_OK) {
+        d->infer_fmt = before;  // the device copy may be half refreshed: the next refresh redoes it
+        return st;
+    }
     if (exponents)
         for (int k = 0; k < 4; ++k) exponents[k] = format == STF_NN_E4M3 ? d->e8[k] : 0;
     return STF_OK;
