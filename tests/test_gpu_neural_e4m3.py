@@ -141,3 +141,23 @@ def test_e4m3_survives_refresh_and_switches_back():
     assert np.median(rel) <= 1e-6 and rel.max() <= 1e-2
     with pytest.raises(stf.StfError):
         stf._check(stf.load().stf_decoder_set_inference(dec.handle, 7, None))
+
+
+def test_e4m3_full_size_sampled():
+    """The c4 decoder's size (2048^2 texels over a 512^2 x 16 latent grid): the scale exponents from
+    the whole grid, and 8192 sampled decodes against the oracle's emulation."""
+    stf, neural = _mods()
+    dec = neural.Decoder(2048, 2048, 512, 512, batch=65536, seed=12)
+    L, P = dec.get_params()
+    L = np.ascontiguousarray(L, np.float32).reshape(512, 512, 16)
+    P = np.ascontiguousarray(P, np.float32)
+    lat16, _, _ = O.nn_pack_inference(L, P)
+    e = dec.set_inference("e4m3")
+    assert e == O.nn_e4m3_scales(lat16, P)
+    rng = np.random.default_rng(12)
+    idx = (rng.integers(0, 2048, 8192) | (rng.integers(0, 2048, 8192) << 16)).astype(np.int32)
+    out = dec.decode(torch.from_numpy(idx).cuda()).cpu().numpy()
+    stf.sync()
+    ref = O.nn_decode_e4m3(lat16, 4, P, idx)
+    bound = e4m3_first_order_bound(lat16.view(np.float16).astype(np.float64), 4, P, idx, e)
+    assert_e4m3_close(out, ref, bound, "e4m3 decode, full size")
