@@ -161,3 +161,21 @@ def test_e4m3_full_size_sampled():
     ref = O.nn_decode_e4m3(lat16, 4, P, idx)
     bound = e4m3_first_order_bound(lat16.view(np.float16).astype(np.float64), 4, P, idx, e)
     assert_e4m3_close(out, ref, bound, "e4m3 decode, full size")
+
+
+def test_e4m3_batch_equals_single_view_renders():
+    """The multi-view kernel runs the same decode pipeline: a batch of views over the E4M3 material
+    renders exactly as the views do one by one."""
+    stf, neural = _mods()
+    dec, L, P = _decoder(neural, tex=256, lat=64, seed=9, scale=0.2)
+    dec.set_inference("e4m3")
+    ntex = dec.texture()
+    views = W.config5_views(n=6, tex=256, seed=7, scale=0.15)
+    mode = O.WAVE3
+    outs = [torch.full((v["height"], v["width"], 4), -1.0, device="cuda") for v in views]
+    stf.render_views([stf.make_view(v, ntex, o) for v, o in zip(views, outs)], stf.FILTER_PER_VIEW, mode, 3)
+    torch.cuda.synchronize()
+    for v, o in zip(views, outs):
+        want, _, _ = stf.render(ntex, v, mode, seed=3)
+        torch.cuda.synchronize()
+        assert torch.equal(o, want)
