@@ -8,11 +8,12 @@
 //     window's clamping lines up, as for WAVE3 in 8 x 4 tiles), each footprint record is read
 //     from shared memory once for both pixels: half the shared-memory wavefronts of the
 //     one-pixel-per-thread path, which the sharing step saturates;
-//   - the two pixels' floating-point work runs as packed f32x2 instructions (FADD2, FMUL2,
-//     FFMA2): coordinates, shading and the neighbour weights of the sharing loop.
-// The texel choice keeps the oracle's operation order exactly: the packed coordinate steps are
-// IEEE round-to-nearest per element (never contracted), and the per-axis selection runs per
-// pixel with the scalar helpers.
+//   - the two pixels' colour work runs as packed f32x2 instructions (FADD2, FMUL2, FFMA2):
+//     shading, and the neighbour weights and channel sums of the sharing loop.
+// The texel choice keeps the oracle's operation order exactly: coordinates and the per-axis
+// selection run per pixel with the scalar, explicitly rounded helpers (a chained packed
+// homography was seen to differ from the scalar chain, so the bit-exact path does not use it).
+// Variants: hash or blue-noise uniforms (BLUE), and exact filtering of the bilinear filter (EX).
 #pragma once
 
 #include <cuda.h>
@@ -212,7 +213,9 @@ template <int KIND> struct GlobalFetch {
 // One pair of pixels of one warp tile: hl in [0, 16) picks column hl % TW and rows 2 (hl / TW)
 // and 2 (hl / TW) + 1; rec holds the tile's 32 lane records (3 x 16 bytes each), wtab (B-spline)
 // its lanes' tap weights, fetch reads a texel (clamp-to-edge). All 16 threads of the half-warp
-// (and of the whole warp) execute every shared-memory step.
+// (and of the whole warp) execute every shared-memory step. BLUE: the selection uniforms come
+// from the blue-noise masks; EX: a pixel whose window holds all four of its bilinear taps
+// returns the full filter over those records (Section 4.2's exact filtering).
 template <int KIND, int F, int MODE, int TW, int TH, bool BLUE = false, bool EX = false, class FETCH = GlobalFetch<KIND>>
 __device__ __forceinline__ void render_pair(const DevView& v, int tx, int ty, int hl, float4* rec, float* wtab,
                                             bool live, const FETCH& fetch)
