@@ -451,7 +451,7 @@ def run_ours(a):
 
 
 def estimators_extra(a, stf, torch, tex, view, flush, rank, out, full):
-    """The estimator comparison of Section 5.2 on the benchmark frame (the reuse mode, 8x4 tiles):
+    """The estimator comparison of Section 5.1 on the benchmark frame (the reuse mode, 8x4 tiles):
     time and PSNR against the full filter of each alternative estimator, plain and clamped."""
     res = {}
     v = dict(view, tile=(8, 4))

@@ -42,13 +42,13 @@ typedef enum {
     STF_ERR_DEVICE_ASSERT = 6  /* a device-side check recorded an out-of-range index */
 } stf_status;
 
-/* Reconstruction filters: bilinear (tent) per Section S5; uniform cubic B-spline per Section
- * 5.5. STF_FILTER_PER_VIEW takes stf_view.filter for each view. */
+/* Reconstruction filters: bilinear (tent) per Section S6; uniform cubic B-spline per Section
+ * 5.4. STF_FILTER_PER_VIEW takes stf_view.filter for each view. */
 typedef enum { STF_FILTER_BILINEAR = 0, STF_FILTER_BSPLINE3 = 1, STF_FILTER_PER_VIEW = -1 } stf_filter;
 
 /* Estimators:
  *   FULL     deterministic filter, every texel under the filter fetched and weighted (the
- *            comparator of Section 5.7);
+ *            comparator of Section 5.6);
  *   ONE_TAP  one-tap STF, the texel drawn by the pixel itself (Section 2.2);
  *   QUAD2    sharing inside aligned 2x2 pixel quads (Table 1 "2x2q");
  *   WAVE2/3/4 square k x k sharing footprints placed per lane inside the warp tile (Section
@@ -326,7 +326,7 @@ const char* stf_last_error(void);
 
 /* ------------------------------------------------------------------------------------------
  * Neural texel decoder (the costly per-texel decode that stochastic filtering amortises,
- * Sections 1 and 5.7: neural texture compression). Not a model from the paper, whose
+ * Sections 1 and 5.6: neural texture compression). Not a model from the paper, whose
  * compressed-material format is not given; the library's small stand-in:
  *   latents: a latent_w x latent_h grid of 16 channels, R = tex_w / latent_w texels per cell
  *            (a power of two <= 16, the same on both axes);
@@ -364,7 +364,7 @@ stf_status stf_decoder_set_params(stf_decoder* d, const float* latent, const flo
 /* Decodes n texels (device array of packed ix | iy << 16) into out (device, n * 8 floats,
  * 16-byte aligned) with the inference kernel. Asynchronous on the library stream. */
 stf_status stf_decoder_decode(const stf_decoder* d, const int32_t* texels, int n, float* out);
-/* Inference precision of a decoder (Section 5.7 names neural texture decompression as the costly
+/* Inference precision of a decoder (Section 5.6 names neural texture decompression as the costly
  * decode that stochastic filtering amortises; the FP8 option is this library's, as the compressed
  * format is not given):
  *   STF_NN_FP16 (the default) as described above;

@@ -9,8 +9,8 @@
  *   - one-tap STF: pick one texel with probability equal to its filter weight (Eq. mc-estimator,
  *     Section 2.2 and the derivation in Section S1);
  *   - texel float coordinates uv * size - 0.5 and the bilinear filter PMF (Section 4.5 listing,
- *     Section S5);
- *   - the uniform cubic B-spline filter (Section 5.5 names it; the kernel is the textbook one);
+ *     Section S6);
+ *   - the uniform cubic B-spline filter (Section 5.4 names it; the kernel is the textbook one);
  *   - sample sharing inside a 32-lane warp tile and the bounded weighted importance sampling
  *     combine w_i = f_c(x_i) / f_i(x_i), result = sum w_i T_i / sum w_j (Eqs. bart-weighted-
  *     estimator, estimator-for-stf, estimator-convex; Section 4.2 and Section 4.5);
@@ -71,7 +71,7 @@ void stf_ref_uniforms(int x, int y, int frame, int view_id, uint64_t seed, float
 
 /* -------------------------------------------------------------- filters */
 
-/* Bilinear (tent) weight per axis: clamp(1 - |d|, 0, 1) (Section S5). */
+/* Bilinear (tent) weight per axis: clamp(1 - |d|, 0, 1) (Section S6). */
 static float w_bilinear(float d)
 {
     float t = 1.0f - fabsf(d);

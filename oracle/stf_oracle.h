@@ -22,7 +22,7 @@
 extern "C" {
 #endif
 
-/* Filters (Section 2.1; bilinear per Section S5, cubic B-spline per Section 5.5). */
+/* Filters (Section 2.1; bilinear per Section S6, cubic B-spline per Section 5.4). */
 enum { REF_BILINEAR = 0, REF_BSPLINE3 = 1 };
 
 /* Sharing modes (Sections 4.3.1, 4.5; Table 1). FULL is the deterministic filter. */

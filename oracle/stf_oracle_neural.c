@@ -1,6 +1,6 @@
 /*
  * CPU oracle for the neural texel decoder (latent grid + MLP) that stands in for the costly
- * per-texel decode STF amortises (neural texture compression, Sections 1 and 5.7).
+ * per-texel decode STF amortises (neural texture compression, Sections 1 and 5.6).
  *
  * TEST INFRASTRUCTURE ONLY (tests, smoke, benchmark CPU leg); shares no code with the GPU.
  *

@@ -134,7 +134,7 @@ template <int F> struct Taps;
 template <> struct Taps<0> { static constexpr int N = 2, K0 = 0; };   // bilinear: floor(c) + {0, 1}
 template <> struct Taps<1> { static constexpr int N = 4, K0 = -1; };  // cubic B-spline: floor(c) + {-1..2}
 
-// Bilinear tent per axis, clamp(1 - |d|, 0, 1) (Section S5). 1 - |d| never exceeds 1, so the
+// Bilinear tent per axis, clamp(1 - |d|, 0, 1) (Section S6). 1 - |d| never exceeds 1, so the
 // clamp is the subtraction's saturation (one instruction; NaN and negative results give +0,
 // as max(., 0) would).
 __device__ __forceinline__ float w_bilinear(float d)

@@ -4,7 +4,7 @@
 // per latent cell): bilinear interpolation of the latent grid at (i + 0.5) / R - 0.5 per axis
 // (clamp-to-edge), 8 position features sin/cos(2 pi phi), sin/cos(4 pi phi) of the phase
 // phi = ((i mod R) + 0.5) / R per axis, then an MLP 24 -> 64 -> 64 -> 8 with ReLU. This is the
-// costly per-texel decode that stochastic filtering amortises (Sections 1 and 5.7).
+// costly per-texel decode that stochastic filtering amortises (Sections 1 and 5.6).
 //
 // Inference precision: latents and weights FP16, the 24 inputs and both hidden layers rounded to
 // FP16, products and biases accumulated in FP32 by the tensor cores, outputs FP32.

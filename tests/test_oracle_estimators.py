@@ -2,7 +2,7 @@
 pairwise MIS, regression; each optionally clamped), pinned against an FP64 enumeration of every
 joint texel selection written here from the estimators' definitions, against the unbiasedness
 the MIS estimators have by construction, and against the ordering of the paper's estimator
-comparison (Section 5.2: the weighted estimator has the lowest error, clamping lowers the error of
+comparison (Section 5.1: the weighted estimator has the lowest error, clamping lowers the error of
 the others, plain importance sampling is worst).
 """
 import itertools
@@ -118,7 +118,7 @@ def test_estimators_by_enumeration(filt, mode):
 
 
 def test_estimator_ordering_on_the_magnified_scene():
-    """Section 5.2 (bilinear, 3x3 footprints, magnified): the weighted estimator has the lowest
+    """Section 5.1 (bilinear, 3x3 footprints, magnified): the weighted estimator has the lowest
     error, clamped regression is close behind, clamping helps IS / MIS / pairwise MIS, and plain IS
     is the worst."""
     mat = W.material_c1()

@@ -660,3 +660,24 @@ def test_shading_matches_textbook_ggx_and_fp32_is_close():
         np.testing.assert_allclose(got[:3], want, rtol=1e-9, atol=1e-12)
         f32 = O.shade(v, [float(np.float32(c)) for c in ch], float(np.float32(u)), float(np.float32(vv)))
         assert np.all(np.abs(f32[:3] - got[:3]) <= 1e-5 * np.maximum(np.abs(got[:3]), 1e-3))
+
+
+def test_reuse_error_falls_with_magnification():
+    """Section 5.1 (error against zoom factor): near a 1:1 texel-to-pixel mapping neighbouring
+    filters barely overlap and the weighted estimator stays close to one-tap STF; as the
+    magnification grows, neighbouring pixels draw from nearly the same distributions and the
+    shared estimate's error falls, while one-tap's stays put."""
+    mat = W.material_c1()
+    gains, reuse = [], []
+    for mag in (1.0, 2.0, 4.0, 8.0):
+        view = W.screen_aligned_view(64, 64, 64, 64, mag, 0, origin=(7.3, 9.1))
+        ex, _ = O.render_exact_f64(mat, view)
+        ps = {}
+        for mode in (O.ONE_TAP, O.WAVE3):
+            mses = [np.mean((O.render(mat, view, mode, seed=s)[0][..., :3] - ex[..., :3]) ** 2) for s in range(6)]
+            ps[mode] = 10 * np.log10(1.0 / np.mean(mses))
+        gains.append(ps[O.WAVE3] - ps[O.ONE_TAP])
+        reuse.append(ps[O.WAVE3])
+    assert all(b > a for a, b in zip(reuse, reuse[1:])), reuse
+    assert all(b > a for a, b in zip(gains, gains[1:])), gains
+    assert gains[0] > 0.0 and gains[-1] > 3 * gains[0]
